@@ -1,0 +1,533 @@
+/*
+ * pt_oracle.c -- FP64 CPU oracle for the transit-model hot path of
+ * Parviainen (2015), "PyTransit: fast and easy exoplanet transit modelling
+ * in Python".
+ *
+ * TEST INFRASTRUCTURE.  This is the plain, slow, obviously-correct
+ * reference that the CUDA library is checked against.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it; the
+ * product path never does.  It shares no code, header, table or helper with
+ * the CUDA library.
+ *
+ * Everything is FP64.  Each function names the passage it follows:
+ *   - Sec. 2.2.1, Eq. (ma_model): quadratic Mandel-Agol flux from
+ *     lambda_e, lambda_d, eta_d.  Those three functions are not printed in
+ *     the paper; they are restated here from Mandel & Agol (2002), Table 1
+ *     and the equations it references (the paper defers to that source).
+ *   - Sec. 2.1.1 Eqs. (gimenez_flux, gimenez_alpha, gimenez), Sec. 2.1.2
+ *     Eq. (ld_general), Sec. 2.1.3 (C_n), Sec. 2.1.4 (A_{n,j} and the Jacobi
+ *     recursion): the Gimenez series model.
+ *   - Sec. 3.2: exposure supersampling.
+ *   - Sec. 1: circular orbits and eccentric orbits solved with Newton's
+ *     method (the paper names the solver but prints no formula).
+ *   - Carlson (1995, Numer. Algorithms 10, 13): symmetric elliptic integrals
+ *     by the duplication theorem, iterated until the arguments agree to
+ *     1e-10 relative, where the remainder is below FP64 resolution.
+ *
+ * Readings of points where the paper is silent (all listed in the design
+ * notes of the repository):
+ *   - Pi(n,k) = int_0^{pi/2} dtheta / ((1 - n sin^2) sqrt(1 - k^2 sin^2)).
+ *   - lambda_d as in Mandel & Agol, with the +2/3 Theta(k - z) term added in
+ *     the flux (Eq. ma_model omits it); eps_d in Eq. (ma_model) is eta_d.
+ *   - G_j(p,q;x) = 2F1(-j, p+j; q; x); the series keeps j = 0 .. n_j-1.
+ *   - t0 is the time of inferior conjunction (true anomaly pi/2 - omega);
+ *     a point behind the star gets z = PTO_Z_BEHIND.
+ *   - Supersamples sit at t + t_exp ((s + 1/2)/n_ss - 1/2), unweighted mean.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PTO_PI 3.14159265358979323846
+#define PTO_Z_BEHIND 1.0e30
+#define PTO_CARLSON_TOL 1e-10
+
+/* ------------------------------------------------------------------------
+ * Carlson symmetric elliptic integrals (Carlson 1995), duplication theorem:
+ *   R_F(x,y,z)   = R_F(x',y',z'),                     x' = (x + lam)/4
+ *   R_D(x,y,z)   = R_D(x',y',z')/4 + 3 / (sqrt(z) (z + lam))
+ *   R_J(x,y,z,p) = R_J(x',y',z',p')/4 + 6 R_C(d^2, d^2 + (p-x)(p-y)(p-z))
+ * with lam = sqrt(xy) + sqrt(yz) + sqrt(zx), d = prod (sqrt p + sqrt x_i).
+ * Iterate until all arguments agree with their (weighted) mean A to 1e-10;
+ * then R(A,...,A) = A^(-1/2) (R_F) or A^(-3/2) (R_D, R_J), whose error is
+ * second order in the spread (~1e-20).
+ * ---------------------------------------------------------------------- */
+double pto_rc(double x, double y)
+{
+    /* R_C(x,y) = (1/2) int_0^inf (t+x)^(-1/2) (t+y)^(-1) dt, x >= 0, y > 0 */
+    if (y > x) return atan(sqrt((y - x) / x)) / sqrt(y - x);
+    if (y < x) return atanh(sqrt((x - y) / x)) / sqrt(x - y);
+    return 1.0 / sqrt(x);
+}
+
+static double max4(double a, double b, double c, double d)
+{
+    return fmax(fmax(a, b), fmax(c, d));
+}
+
+double pto_rf(double x, double y, double z)
+{
+    for (int it = 0; it < 200; ++it) {
+        double A = (x + y + z) / 3.0;
+        double dev = max4(fabs(x - A), fabs(y - A), fabs(z - A), 0.0);
+        if (dev <= PTO_CARLSON_TOL * A) return 1.0 / sqrt(A);
+        double sx = sqrt(x), sy = sqrt(y), sz = sqrt(z);
+        double lam = sx * sy + sy * sz + sz * sx;
+        x = 0.25 * (x + lam);
+        y = 0.25 * (y + lam);
+        z = 0.25 * (z + lam);
+    }
+    return NAN;
+}
+
+double pto_rd(double x, double y, double z)
+{
+    double sum = 0.0, fac = 1.0;
+    for (int it = 0; it < 200; ++it) {
+        double A = (x + y + 3.0 * z) / 5.0;
+        double dev = max4(fabs(x - A), fabs(y - A), fabs(z - A), 0.0);
+        if (dev <= PTO_CARLSON_TOL * A) return sum + fac / (A * sqrt(A));
+        double sx = sqrt(x), sy = sqrt(y), sz = sqrt(z);
+        double lam = sx * sy + sy * sz + sz * sx;
+        sum += fac * 3.0 / (sz * (z + lam));
+        fac *= 0.25;
+        x = 0.25 * (x + lam);
+        y = 0.25 * (y + lam);
+        z = 0.25 * (z + lam);
+    }
+    return NAN;
+}
+
+double pto_rj(double x, double y, double z, double p)
+{
+    double sum = 0.0, fac = 1.0;
+    for (int it = 0; it < 200; ++it) {
+        double A = (x + y + z + 2.0 * p) / 5.0;
+        double dev = max4(fabs(x - A), fabs(y - A), fabs(z - A), fabs(p - A));
+        if (dev <= PTO_CARLSON_TOL * A) return sum + fac / (A * sqrt(A));
+        double sx = sqrt(x), sy = sqrt(y), sz = sqrt(z), sp = sqrt(p);
+        double lam = sx * sy + sy * sz + sz * sx;
+        double d = (sp + sx) * (sp + sy) * (sp + sz);
+        sum += fac * 6.0 * pto_rc(d * d, d * d + (p - x) * (p - y) * (p - z));
+        fac *= 0.25;
+        x = 0.25 * (x + lam);
+        y = 0.25 * (y + lam);
+        z = 0.25 * (z + lam);
+        p = 0.25 * (p + lam);
+    }
+    return NAN;
+}
+
+/* Complete elliptic integrals of parameter m = k^2, passed together with its
+ * complement mc = 1 - m (callers form mc from factored geometry so that it
+ * keeps full relative precision near m -> 1). */
+double pto_ellk(double mc) { return pto_rf(0.0, mc, 1.0); }
+
+double pto_elle(double m, double mc)
+{
+    return pto_rf(0.0, mc, 1.0) - m / 3.0 * pto_rd(0.0, mc, 1.0);
+}
+
+/* Pi(n | m) = int_0^{pi/2} dth / ((1 - n sin^2 th) sqrt(1 - m sin^2 th)),
+ * for n < 1, written through rho = 1 - n > 0 as
+ *   int (cos^2 + sin^2) / ((cos^2 + rho sin^2) sqrt(cos^2 + mc sin^2))
+ * and each half as a positive R_J (cot^2 substitution, then the
+ * complementary angle and homogeneity for the cos^2 half):
+ *   = R_J(0, 1/mc, 1, 1/rho) / (3 rho sqrt(mc)) + R_J(0, mc, 1, rho) / 3.
+ * Both terms are positive, so there is no cancellation when n -> -inf
+ * (the z -> k neighbourhood of Mandel & Agol's lambda_1 and lambda_2). */
+double pto_ellpi(double n, double mc)
+{
+    double rho = 1.0 - n;
+    return pto_rj(0.0, 1.0 / mc, 1.0, 1.0 / rho) / (3.0 * rho * sqrt(mc)) +
+           pto_rj(0.0, mc, 1.0, rho) / 3.0;
+}
+
+/* ------------------------------------------------------------------------
+ * Mandel & Agol (2002) quadratic-law terms (Sec. 2.2.1, Eq. ma_model).
+ * ---------------------------------------------------------------------- */
+
+/* Geometry of the partial overlap: the triangle with sides 1 (star radius),
+ * p (planet radius) and z (centre distance).  kap1 and kap0 are its angles
+ * at the star and planet centres (half-angles of the chord through the two
+ * intersection points).  The law of cosines gives their cosines and the
+ * triangle area A their sines (sin kap1 = 2A/z, sin kap0 = 2A/(pz)); A comes
+ * from Heron's formula in the factored form
+ *   16 A^2 = (1 - (z-p)^2) ((z+p)^2 - 1) = 4 z^2 - (1 + z^2 - p^2)^2,
+ * and atan2 keeps full precision at the contact points z = 1 -+ p, where an
+ * acos of the rounded cosine would lose half the digits. */
+static void overlap_geometry(double p, double z, double *kap0, double *kap1, double *four_a)
+{
+    double d = (z - 1.0) + p;                         /* z + p - 1 */
+    double oma = (1.0 - z + p) * (1.0 + z - p);       /* 1 - (z-p)^2 */
+    double bm1 = d * (1.0 + z + p);                   /* (z+p)^2 - 1 */
+    double fa = sqrt(fmax(0.0, oma * bm1));
+    *four_a = fa;
+    *kap1 = atan2(fa, 1.0 - p * p + z * z);
+    *kap0 = atan2(fa, p * p + z * z - 1.0);
+}
+
+/* lambda_e: fraction of a uniform unit disk covered by a disk of radius p at
+ * centre distance z (the lens area over pi):
+ *   (p^2 kap0 + kap1 - sqrt(4 z^2 - (1 + z^2 - p^2)^2) / 2) / pi. */
+double pto_lambda_e(double p, double z)
+{
+    z = fabs(z);
+    if (p <= 0.0 || z >= 1.0 + p) return 0.0;
+    if (p >= 1.0 && z <= p - 1.0) return 1.0;
+    if ((z - 1.0) + p <= 0.0) return p * p;
+    double kap0, kap1, fa;
+    overlap_geometry(p, z, &kap0, &kap1, &fa);
+    return (p * p * kap0 + kap1 - 0.5 * fa) / PTO_PI;
+}
+
+/* out[0] = lambda_e, out[1] = lambda_d (without the 2/3 Theta(p-z) term),
+ * out[2] = eta_d.  Case numbers are those of Mandel & Agol (2002) Table 1;
+ * equality tests are exact, as in that table. */
+void pto_ma_terms(double p, double z, double *out)
+{
+    const double pi = PTO_PI;
+    z = fabs(z);
+    out[0] = out[1] = out[2] = 0.0;
+    if (p <= 0.0 || z >= 1.0 + p) return;              /* case 1 */
+    if (p >= 1.0 && z <= p - 1.0) {                    /* case 11: star covered */
+        out[0] = 1.0; out[1] = 0.0; out[2] = 0.5;
+        return;
+    }
+    out[0] = pto_lambda_e(p, z);
+
+    /* q and the Pi parameters are formed from differences taken once, so
+     * that they keep their relative precision as z -> p (a -> 0):
+     * q = p^2 - z^2 = (p - z)(p + z), a - b = -4zp, a - 1 = -(1 - a). */
+    double a = (z - p) * (z - p), b = (z + p) * (z + p), q = (p - z) * (p + z);
+    /* d = z + p - 1 decides inside (d < 0), contact with the limb (d == 0)
+     * and partial (d > 0); 1 - b and b - 1 are formed from it so that the
+     * branch and the sign of the elliptic parameter always agree. */
+    double d = (z - 1.0) + p;
+    double oma = (1.0 - z + p) * (1.0 + z - p);   /* 1 - a */
+    double omb = -d * (1.0 + z + p);              /* 1 - b */
+    double bm1 = d * (1.0 + z + p);               /* b - 1 */
+    double eta2 = 0.5 * p * p * (p * p + 2.0 * z * z);
+    double ld, ed;
+
+    if (z == 0.0) {                                    /* case 10: lambda_6 */
+        ld = -2.0 / 3.0 * pow(1.0 - p * p, 1.5);
+        ed = eta2;
+    } else if (p == 0.5 && z == 0.5) {                 /* case 6 */
+        ld = 1.0 / 3.0 - 4.0 / (9.0 * pi);
+        ed = 3.0 / 32.0;
+    } else if (z == p) {
+        if (p < 0.5) {                                 /* case 5: lambda_4, modulus 2p */
+            double m = 4.0 * p * p, mc = (1.0 - 2.0 * p) * (1.0 + 2.0 * p);
+            ld = 1.0 / 3.0 + 2.0 / (9.0 * pi) *
+                 (4.0 * (2.0 * p * p - 1.0) * pto_elle(m, mc) + (1.0 - 4.0 * p * p) * pto_ellk(mc));
+            ed = eta2;
+        } else {                                       /* case 7: lambda_3, modulus 1/(2p) */
+            double m = 1.0 / (4.0 * p * p), mc = (2.0 * p - 1.0) * (2.0 * p + 1.0) / (4.0 * p * p);
+            ld = 1.0 / 3.0 + 16.0 * p / (9.0 * pi) * (2.0 * p * p - 1.0) * pto_elle(m, mc) -
+                 (1.0 - 4.0 * p * p) * (3.0 - 8.0 * p * p) / (9.0 * pi * p) * pto_ellk(mc);
+            double kap0, kap1, fa;
+            overlap_geometry(p, z, &kap0, &kap1, &fa);
+            ed = (kap1 + 2.0 * eta2 * kap0 - 0.25 * (1.0 + 5.0 * p * p + z * z) * fa) / (2.0 * pi);
+        }
+    } else if (d == 0.0) {                             /* case 4: lambda_5, z = 1 - p */
+        ld = 2.0 / (3.0 * pi) * acos(1.0 - 2.0 * p) -
+             4.0 / (9.0 * pi) * (3.0 + 2.0 * p - 8.0 * p * p) * sqrt(p * (1.0 - p)) -
+             (p > 0.5 ? 2.0 / 3.0 : 0.0);
+        ed = eta2;
+    } else if (d < 0.0) {                              /* cases 3, 9: lambda_2 */
+        double m = 4.0 * z * p / oma, mc = omb / oma;
+        double K = pto_ellk(mc), E = pto_elle(m, mc), P = pto_ellpi(-4.0 * z * p / a, mc);
+        ld = 2.0 / (9.0 * pi * sqrt(oma)) *
+             ((1.0 - 5.0 * z * z + p * p + q * q) * K + oma * (z * z + 7.0 * p * p - 4.0) * E - 3.0 * q / a * P);
+        ed = eta2;
+    } else {                                           /* cases 2, 8: lambda_1, eta_1 */
+        double m = oma / (4.0 * z * p), mc = bm1 / (4.0 * z * p);
+        double K = pto_ellk(mc), E = pto_elle(m, mc), P = pto_ellpi(-oma / a, mc);
+        ld = 1.0 / (9.0 * pi * sqrt(p * z)) *
+             (((1.0 - b) * (2.0 * b + a - 3.0) - 3.0 * q * (b - 2.0)) * K +
+              4.0 * p * z * (z * z + 7.0 * p * p - 4.0) * E - 3.0 * q / a * P);
+        double kap0, kap1, fa;     /* fa = 4A = sqrt((1 - a)(b - 1)) */
+        overlap_geometry(p, z, &kap0, &kap1, &fa);
+        ed = (kap1 + 2.0 * eta2 * kap0 - 0.25 * (1.0 + 5.0 * p * p + z * z) * fa) / (2.0 * pi);
+    }
+    out[1] = ld;
+    out[2] = ed;
+}
+
+/* Eq. (ma_model) with a = u1, b = u2, c = u1 + 2 u2, eps_d read as eta_d and
+ * Mandel & Agol's 2/3 Theta(p - z) term restored. */
+double pto_flux_quad(double p, double z, double u1, double u2)
+{
+    double t[3];
+    pto_ma_terms(p, z, t);
+    double c = u1 + 2.0 * u2;
+    double th = (p > fabs(z)) ? 2.0 / 3.0 : 0.0;
+    if (t[0] == 0.0 && t[1] == 0.0 && t[2] == 0.0) return 1.0;
+    return 1.0 - ((1.0 - c) * t[0] + c * (t[1] + th) + u2 * t[2]) / (1.0 - u1 / 3.0 - u2 / 6.0);
+}
+
+/* ------------------------------------------------------------------------
+ * Gimenez (2006) series, Sec. 2.1.
+ * ---------------------------------------------------------------------- */
+
+/* G_j(p,q;x) = 2F1(-j, p+j; q; x) for j = 0..n-1 by the Jacobi three-term
+ * recurrence (Sec. 2.1.4).  With s = 2j + p:
+ *   2(j+p)(s-1)(q+j) G_{j+1} =
+ *       s[(s+1)(s-1)(1-2x) + (q-1)^2 - (p-q)^2] G_j - 2j(j+p-q)(s+1) G_{j-1},
+ * the standard recurrence of P_j^{(q-1,p-q)}(1-2x) rescaled by j!/(q)_j. */
+void pto_jacobi_g(int n, double p, double q, double x, double *g)
+{
+    if (n <= 0) return;
+    g[0] = 1.0;
+    if (n == 1) return;
+    g[1] = 1.0 - (p + 1.0) * x / q;
+    for (int j = 1; j + 1 < n; ++j) {
+        double s = 2.0 * j + p;
+        double j1 = s * ((s + 1.0) * (s - 1.0) + (q - 1.0) * (q - 1.0) - (p - q) * (p - q));
+        double j2 = -2.0 * s * (s + 1.0) * (s - 1.0);
+        double j3 = -2.0 * j * (j + p - q) * (s + 1.0);
+        double j4 = 2.0 * (j + p) * (s - 1.0) * (q + j);
+        g[j + 1] = ((j1 + j2 * x) * g[j] + j3 * g[j - 1]) / j4;
+    }
+}
+
+/* Eq. (gimemez_a): A_{n,j} = (-1)^j (2j+nu+2) Gamma(nu+j+1) / (nu Gamma(nu+1) Gamma(j+2)). */
+double pto_gimenez_a(int n, int j)
+{
+    double nu = 0.5 * (n + 2);
+    double sgn = (j % 2) ? -1.0 : 1.0;
+    return sgn * (2.0 * j + nu + 2.0) / nu * exp(lgamma(nu + j + 1.0) - lgamma(nu + 1.0) - lgamma(j + 2.0));
+}
+
+/* Eq. (gimenez): alpha_n(b,c) for n = 0..N with b = k/(1+k), c = z/(1+k),
+ * series truncated to n_j terms. */
+void pto_gimenez_alpha(int N, int n_j, double k, double z, double *alpha)
+{
+    z = fabs(z);
+    for (int n = 0; n <= N; ++n) alpha[n] = 0.0;
+    if (k <= 0.0 || z >= 1.0 + k || n_j <= 0) return;
+    double b = k / (1.0 + k), c = z / (1.0 + k);
+    double *g1 = (double *)malloc(sizeof(double) * (size_t)n_j);
+    double *g2 = (double *)malloc(sizeof(double) * (size_t)n_j);
+    for (int n = 0; n <= N; ++n) {
+        double nu = 0.5 * (n + 2);
+        pto_jacobi_g(n_j, nu + 2.0, nu + 1.0, 1.0 - b, g1);
+        pto_jacobi_g(n_j, nu + 2.0, 1.0, c * c, g2);
+        double s = 0.0;
+        for (int j = 0; j < n_j; ++j) s += pto_gimenez_a(n, j) * g1[j] * g1[j] * g2[j];
+        alpha[n] = b * b * pow(1.0 - c * c, nu + 1.0) * s;
+    }
+    free(g1);
+    free(g2);
+}
+
+/* Eqs. (gimenez_flux, gimenez_alpha) with the C_n of Sec. 2.1.3;
+ * u[0..N-1] holds u_1..u_N of Eq. (ld_general). */
+double pto_flux_gimenez(int N, int n_j, double k, double z, const double *u)
+{
+    double alpha[64];
+    if (N > 63) return NAN;
+    pto_gimenez_alpha(N, n_j, k, z, alpha);
+    double su = 0.0, sd = 0.0;
+    for (int n = 1; n <= N; ++n) {
+        su += u[n - 1];
+        sd += n * u[n - 1] / (n + 2.0);
+    }
+    double D = 1.0 - sd;
+    double a = (1.0 - su) / D * alpha[0];
+    for (int n = 1; n <= N; ++n) a += u[n - 1] / D * alpha[n];
+    return 1.0 - a;
+}
+
+/* ------------------------------------------------------------------------
+ * Orbits (Sec. 1: circular orbits; eccentric orbits by Newton's method).
+ * ---------------------------------------------------------------------- */
+
+/* Circular orbit: phase phi = 2 pi (t - t0)/P from conjunction,
+ * z = a sqrt(sin^2 phi + cos^2 i cos^2 phi); behind the star if cos phi <= 0. */
+double pto_z_circ(double t, double t0, double P, double a, double inc)
+{
+    double x = (t - t0) / P;
+    x -= rint(x);
+    double ph = 2.0 * PTO_PI * x;
+    double cp = cos(ph), sp = sin(ph), ci = cos(inc);
+    if (cp <= 0.0) return PTO_Z_BEHIND;
+    return a * sqrt(sp * sp + ci * ci * cp * cp);
+}
+
+/* Kepler's equation E - e sin E = M by Newton's method; returns iterations
+ * used, or -1 if |dE| did not fall below tol within max_iter.  M is first
+ * reduced to [0, 2 pi); the start E = M (e < 0.8) or E = pi (the inflection
+ * point of E - e sin E, from which Newton's iterates are monotone) follows
+ * the usual practice.  The returned E is shifted back by the same multiple
+ * of 2 pi. */
+int pto_kepler_newton(double M, double e, int max_iter, double tol, double *E_out)
+{
+    double shift = 2.0 * PTO_PI * floor(M / (2.0 * PTO_PI));
+    double Mr = M - shift;
+    double E = (e < 0.8) ? Mr : PTO_PI;
+    for (int it = 1; it <= max_iter; ++it) {
+        double d = (E - e * sin(E) - Mr) / (1.0 - e * cos(E));
+        E -= d;
+        if (fabs(d) < tol) {
+            *E_out = E + shift;
+            return it;
+        }
+    }
+    *E_out = E + shift;
+    return -1;
+}
+
+/* Eccentric orbit: mean anomaly M = M_tr + 2 pi (t - t0)/P where M_tr is the
+ * mean anomaly at true anomaly f_tr = pi/2 - omega; Newton for E; true anomaly
+ * f; r = a (1 - e cos E); z = r sqrt(cos^2(w+f) + sin^2(w+f) cos^2 i);
+ * behind the star if sin(w+f) <= 0.  *status is set to -1 on non-convergence. */
+double pto_z_ecc(double t, double t0, double P, double a, double inc, double e, double w,
+                 int max_iter, double tol, int *status)
+{
+    double ftr = 0.5 * PTO_PI - w;
+    double Etr = 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * ftr), sqrt(1.0 + e) * cos(0.5 * ftr));
+    double Mtr = Etr - e * sin(Etr);
+    double x = (t - t0) / P;
+    x -= rint(x);
+    double M = Mtr + 2.0 * PTO_PI * x;
+    double E;
+    int it = pto_kepler_newton(M, e, max_iter, tol, &E);
+    if (status) *status = (it < 0) ? -1 : 0;
+    double f = 2.0 * atan2(sqrt(1.0 + e) * sin(0.5 * E), sqrt(1.0 - e) * cos(0.5 * E));
+    double r = a * (1.0 - e * cos(E));
+    double s = sin(w + f), c = cos(w + f), ci = cos(inc);
+    if (s <= 0.0) return PTO_Z_BEHIND;
+    return r * sqrt(c * c + s * s * ci * ci);
+}
+
+/* Impact parameter to inclination (Winn 2010 convention):
+ * b = a cos i (1 - e^2) / (1 + e sin w). */
+double pto_inc_from_b(double b, double a, double e, double w)
+{
+    return acos(b / a * (1.0 + e * sin(w)) / (1.0 - e * e));
+}
+
+/* ------------------------------------------------------------------------
+ * Batched drivers: flux cube [v][b][t] with supersampling (Sec. 3.2) and the
+ * multi-passband evaluation of Secs. 2.1.3 and 2.2.2 (here simply evaluated
+ * per passband: the oracle does no factoring of its own).
+ * e == NULL selects the circular orbit.  k is [v] or, if k_per_band, [v][b].
+ * ---------------------------------------------------------------------- */
+static double orbit_z(const double *t0, const double *P, const double *a, const double *inc,
+                      const double *e, const double *w, int v, double tt, int *bad)
+{
+    if (!e) return pto_z_circ(tt, t0[v], P[v], a[v], inc[v]);
+    int st = 0;
+    double z = pto_z_ecc(tt, t0[v], P[v], a[v], inc[v], e[v], w[v], 50, 1e-14, &st);
+    if (st) *bad = 1;
+    return z;
+}
+
+int pto_z_batch(const double *t, int n_t, const double *t0, const double *P, const double *a,
+                const double *inc, const double *e, const double *w, int n_v, int n_ss, double t_exp,
+                double *z /* [v][t*n_ss + s] */)
+{
+    int nbad = 0;
+    for (int v = 0; v < n_v; ++v)
+        for (int i = 0; i < n_t; ++i)
+            for (int s = 0; s < n_ss; ++s) {
+                double tt = t[i] + t_exp * ((s + 0.5) / n_ss - 0.5);
+                int bad = 0;
+                z[((size_t)v * n_t + i) * n_ss + s] = orbit_z(t0, P, a, inc, e, w, v, tt, &bad);
+                nbad += bad;
+            }
+    return nbad;
+}
+
+int pto_lc_ma(const double *t, int n_t, const double *t0, const double *P, const double *a,
+              const double *inc, const double *e, const double *w, int n_v, const double *k,
+              int k_per_band, const double *ld /* [v][b][2] */, int n_b, int n_ss, double t_exp,
+              double *flux /* [v][b][t] */, int n_threads)
+{
+    int nbad = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#endif
+    for (int v = 0; v < n_v; ++v) {
+        for (int i = 0; i < n_t; ++i) {
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] = 0.0;
+            for (int s = 0; s < n_ss; ++s) {
+                double tt = t[i] + t_exp * ((s + 0.5) / n_ss - 0.5);
+                int bad = 0;
+                double z = orbit_z(t0, P, a, inc, e, w, v, tt, &bad);
+                nbad += bad;
+                for (int b = 0; b < n_b; ++b) {
+                    double kk = k_per_band ? k[(size_t)v * n_b + b] : k[v];
+                    const double *u = ld + ((size_t)v * n_b + b) * 2;
+                    flux[((size_t)v * n_b + b) * n_t + i] += pto_flux_quad(kk, z, u[0], u[1]);
+                }
+            }
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] /= n_ss;
+        }
+    }
+    return nbad;
+}
+
+int pto_lc_gimenez(const double *t, int n_t, const double *t0, const double *P, const double *a,
+                   const double *inc, const double *e, const double *w, int n_v, const double *k,
+                   int k_per_band, const double *ld /* [v][b][N] */, int N, int n_b, int n_j, int n_ss,
+                   double t_exp, double *flux /* [v][b][t] */, int n_threads)
+{
+    int nbad = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#endif
+    for (int v = 0; v < n_v; ++v) {
+        for (int i = 0; i < n_t; ++i) {
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] = 0.0;
+            for (int s = 0; s < n_ss; ++s) {
+                double tt = t[i] + t_exp * ((s + 0.5) / n_ss - 0.5);
+                int bad = 0;
+                double z = orbit_z(t0, P, a, inc, e, w, v, tt, &bad);
+                nbad += bad;
+                for (int b = 0; b < n_b; ++b) {
+                    double kk = k_per_band ? k[(size_t)v * n_b + b] : k[v];
+                    const double *u = ld + ((size_t)v * n_b + b) * N;
+                    flux[((size_t)v * n_b + b) * n_t + i] += pto_flux_gimenez(N, n_j, kk, z, u);
+                }
+            }
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] /= n_ss;
+        }
+    }
+    return nbad;
+}
+
+/* Sum of squared residuals per (vector, passband): sum_t w (y - f)^2, the
+ * likelihood reduction the paper moves onto the device (Sec. 3.4).
+ * y and wt are [b][t]; wt == NULL means unit weights. */
+void pto_ssr(const double *flux, const double *y, const double *wt, int n_v, int n_b, int n_t,
+             double *ssr)
+{
+    for (int v = 0; v < n_v; ++v)
+        for (int b = 0; b < n_b; ++b) {
+            double s = 0.0;
+            for (int i = 0; i < n_t; ++i) {
+                double r = y[(size_t)b * n_t + i] - flux[((size_t)v * n_b + b) * n_t + i];
+                s += (wt ? wt[(size_t)b * n_t + i] : 1.0) * r * r;
+            }
+            ssr[(size_t)v * n_b + b] = s;
+        }
+}
+
+int pto_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
