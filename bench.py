@@ -1,0 +1,351 @@
+"""Benchmark: flux points per second of the transit-model hot path on GB300.
+
+Workload (one step): the long-cadence series -- 50,000 exposure times over
+1,000 d, 29.4-min exposures supersampled x10, 256 eccentric parameter vectors
+drawn from the seeded priors, one passband -- evaluated with BOTH models:
+quadratic Mandel-Agol (pt_ma_quad) and the Gimenez series with 8
+general-law coefficients and n_j = 128 Jacobi terms (pt_gimenez).  A flux
+point is one (exposure time, parameter vector, passband) output; a step
+produces 2 x 50,000 x 256 of them.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launching stream; between steps a 256 MiB buffer is written to flush
+L2 (outside the events).  Barrier + synchronize on both sides; the max over
+ranks is reported.  Under torchrun every rank runs its own replica (the path
+has no exchange step), so scaling is weak.
+
+--impl reference times the FP64 oracle (the CPU reference) on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "flux points/sec (time×sample×passband) on 1 GB300 at ≤1e-5 max abs error vs FP64"
+UNIT = "flux points/s"
+N_LD = 8
+N_J = 128
+SAMPLE_V = 16            # vectors in the CPU-oracle sample
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        self.proc = subprocess.Popen([exe, "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _oracle_sample(wl, n_v, n_t=None):
+    """Inputs of the first n_v vectors (and optionally the first n_t times),
+    with the FP32 parameters the GPU sees widened to FP64."""
+    f32 = lambda x: None if x is None else np.asarray(x, np.float32).astype(np.float64)
+    sl = slice(0, n_v)
+    o = wl["orbit"]
+    orb = dict(t0=np.asarray(o["t0"])[sl], P=np.asarray(o["P"])[sl], a=f32(o["a"][sl]), inc=f32(o["inc"][sl]),
+               e=f32(o["e"][sl]), w=f32(o["w"][sl]))
+    t = wl["t"] if n_t is None else wl["t"][:n_t]
+    return t, orb, f32(wl["k"][sl]), f32(wl["ld"][sl]), f32(wl["ld_gim"][sl])
+
+
+def run_oracle_step(wl, n_v, n_t=None):
+    """One oracle pass (both models) over a sample; returns (seconds, flux points, (fm, fg))."""
+    import oracle
+    t, orb, k, ld, ldg = _oracle_sample(wl, n_v, n_t)
+    t0 = time.perf_counter()
+    fm, _ = oracle.lc_ma(t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+    fg, _ = oracle.lc_gimenez(t, orb, k, ldg, N_J, n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+    dt = time.perf_counter() - t0
+    return dt, fm.size + fg.size, (fm, fg)
+
+
+def reference_main(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1504_07433_gb300 import workloads as W
+    import oracle
+    oracle.build()
+    wl = W.long_cadence()
+    n_t_sample = 12500
+    for _ in range(args.warmup):
+        run_oracle_step(wl, SAMPLE_V, n_t_sample)
+    times, pts = [], 0
+    for _ in range(args.steps):
+        dt, p, _ = run_oracle_step(wl, SAMPLE_V, n_t_sample)
+        times.append(dt)
+        pts = p
+    tot = float(np.sum(times))
+    value = pts * args.steps / tot
+    sample = "%d vectors x first %d times x %d supersamples, MA + Gimenez(N=%d, n_j=%d), per step" % (
+        SAMPLE_V, n_t_sample, wl["n_ss"], N_LD, N_J)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "models": "MA quadratic + Gimenez N=%d n_j=%d" % (N_LD, N_J),
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1504_07433_gb300 as pt
+    from paper_1504_07433_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pt.load_library(build_if_missing=True)
+
+    wl = W.long_cadence()
+    n_t, n_v, n_ss = wl["t"].size, wl["k"].size, wl["n_ss"]
+    t = torch.as_tensor(wl["t"], dtype=torch.float64, device=dev)
+    orb = pt.orbit_to_device(wl["orbit"], dev)
+    k = torch.as_tensor(wl["k"], dtype=torch.float32, device=dev)
+    ld = torch.as_tensor(wl["ld"], dtype=torch.float32, device=dev)
+    ldg = torch.as_tensor(wl["ld_gim"], dtype=torch.float32, device=dev)
+    plan = pt.GimenezPlan(N_LD, N_J)
+    fm = torch.empty((n_v, 1, n_t), dtype=torch.float32, device=dev)
+    fg = torch.empty_like(fm)
+    wm = torch.empty(pt.ma_quad_work_bytes(n_t, n_v, 1), dtype=torch.uint8, device=dev)
+    wg = torch.empty(plan.work_bytes(n_t, n_v, 1), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pt.ma_quad(t, orb, k, ld, n_ss=n_ss, t_exp=wl["t_exp"], work=wm, flux=fm)
+        pt.gimenez(plan, t, orb, k, ldg, n_ss=n_ss, t_exp=wl["t_exp"], work=wg, flux=fg)
+
+    # algorithmic work: in-transit (time, supersample, vector) evaluations, from the FP64-Newton z kernel
+    zz, _ = pt.z_ecc(t, orb, n_ss=n_ss, t_exp=wl["t_exp"])
+    n_intr = int((zz < (1.0 + k[:, None])).sum().item())
+    del zz
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        pt.ma_quad(t, orb, k, ld, n_ss=n_ss, t_exp=wl["t_exp"], work=wm, flux=fm)
+        ev[i][1].record(stream)
+        pt.gimenez(plan, t, orb, k, ldg, n_ss=n_ss, t_exp=wl["t_exp"], work=wg, flux=fg)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    ma_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
+    g_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
+    step_ms = float(np.sum(ma_ms) + np.sum(g_ms)) / K
+    tmax = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    step_ms = float(tmax.item())
+    pts_per_step = 2 * n_t * n_v * 1
+    value = pts_per_step * ws / (step_ms * 1e-3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_t = torch.as_tensor(wl["t"], dtype=torch.float64).pin_memory()
+        host_par = {kk: torch.as_tensor(np.asarray(v), dtype=(torch.float64 if kk in ("t0", "P") else torch.float32)
+                                        ).pin_memory()
+                    for kk, v in wl["orbit"].items() if kk in ("t0", "P", "a", "inc", "e", "w")}
+        host_k = torch.as_tensor(wl["k"], dtype=torch.float32).pin_memory()
+        host_ld = torch.as_tensor(wl["ld"], dtype=torch.float32).pin_memory()
+        host_ldg = torch.as_tensor(wl["ld_gim"], dtype=torch.float32).pin_memory()
+        out_m = torch.empty(fm.shape, dtype=torch.float32).pin_memory()
+        out_g = torch.empty(fg.shape, dtype=torch.float32).pin_memory()
+        dev_par = {kk: torch.empty_like(v, device=dev) for kk, v in host_par.items()}
+        t_d, k_d, ld_d, ldg_d = (torch.empty_like(x, device=dev) for x in (host_t, host_k, host_ld, host_ldg))
+        h2d = sum(x.numel() * x.element_size() for x in [host_t, host_k, host_ld, host_ldg] + list(host_par.values()))
+        d2h = out_m.numel() * 4 + out_g.numel() * 4
+
+        def e2e_step():
+            t_d.copy_(host_t, non_blocking=True)
+            for kk in dev_par:
+                dev_par[kk].copy_(host_par[kk], non_blocking=True)
+            k_d.copy_(host_k, non_blocking=True)
+            ld_d.copy_(host_ld, non_blocking=True)
+            ldg_d.copy_(host_ldg, non_blocking=True)
+            o = dict(dev_par)
+            pt.ma_quad(t_d, o, k_d, ld_d, n_ss=n_ss, t_exp=wl["t_exp"], work=wm, flux=fm)
+            pt.gimenez(plan, t_d, o, k_d, ldg_d, n_ss=n_ss, t_exp=wl["t_exp"], work=wg, flux=fg)
+            out_m.copy_(fm, non_blocking=True)
+            out_g.copy_(fg, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / K
+        em = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(em, op=dist.ReduceOp.MAX)
+        e2e = {"value": pts_per_step * ws / (float(em.item()) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": float(em.item())}
+
+    # roofline of the dominant kernel (the Gimenez series evaluation):
+    # algorithmic FP32 flops = 7 per (n, j) recursion step per in-transit evaluation
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    g_mean_ms = float(np.mean(g_ms))
+    flops = 7.0 * (N_LD + 1) * (N_J - 1) * n_intr
+    achieved = flops / (g_mean_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "gim_lc_kernel (pt_gimenez call: set-up + table + series kernels)",
+                "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": None,
+                "peak_source": "FP32 lanes 152 SM x 128 x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_max, peak_src),
+                "algorithmic_flops_per_launch": flops, "in_transit_evaluations": n_intr}
+
+    cpu = None
+    max_err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        dt, p, (rm, rg) = run_oracle_step(wl, SAMPLE_V)
+        gm = fm[:SAMPLE_V].cpu().numpy().astype(np.float64)
+        gg = fg[:SAMPLE_V].cpu().numpy().astype(np.float64)
+        max_err = {"ma": float(np.max(np.abs(gm - rm))), "gimenez": float(np.max(np.abs(gg - rg))),
+                   "sample": "first %d vectors, all times" % SAMPLE_V}
+        cpu = {"value": p / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": "%d of %d vectors x %d times x %d supersamples, MA + Gimenez(N=%d, n_j=%d): %.1f s"
+                         % (SAMPLE_V, n_v, n_t, n_ss, N_LD, N_J, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+                "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["name"], "models": "MA quadratic + Gimenez N=%d n_j=%d" % (N_LD, N_J),
+                           "n_t": n_t, "n_v": n_v, "n_ss": n_ss, "n_b": 1, "flux_points_per_step": pts_per_step,
+                           "l2": "flushed between timed steps (256 MiB write outside the events)",
+                           "parallelism": "replicas x%d" % ws},
+                "components_ms": {"ma_quad": float(np.mean(ma_ms)), "gimenez": g_mean_ms},
+                "max_abs_err_vs_oracle": max_err,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 5 * K, "clocks": clocks, "wall_s_timed": wall}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * pt.h -- C ABI of the GB300 (sm_103a) transit-model library.
+ *
+ * The library evaluates the forward model of Parviainen (2015), "PyTransit:
+ * fast and easy exoplanet transit modelling in Python": quadratic
+ * Mandel-Agol fluxes (Sec. 2.2, Eq. ma_model) and Gimenez series fluxes
+ * (Sec. 2.1, Eqs. gimenez_flux, gimenez_alpha, gimenez) over
+ * time points x parameter vectors x passbands, with exposure supersampling
+ * (Sec. 3.2), circular or eccentric orbits (Sec. 1), limb darkening factored
+ * out of the geometry (Secs. 2.1.3, 2.2.2) and, optionally, the likelihood
+ * reduction moved onto the device (Sec. 3.4).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev / documented "device" are device (GPU) pointers,
+ *     owned by the caller.  The library never frees them.  Entry points do
+ *     not allocate device memory unless their comment says so (the Gimenez
+ *     plan owns its coefficient tables).
+ *   - `stream` is a cudaStream_t (0 = legacy default stream).  Calls are
+ *     asynchronous with respect to the host: they enqueue kernels and return.
+ *   - Return value: PT_OK, or a PT_ERR_* code for a host-detected error (bad
+ *     size, null pointer, workspace too small) or a launch error.  A launch
+ *     error's text is available from pt_last_error_string() (thread-local).
+ *     Errors detected on the device (Newton not converged) are counted in an
+ *     optional caller-provided device int, read after the stream syncs.
+ *   - Layouts are row-major with time fastest: a flux cube is [n_v][n_b][n_t].
+ *   - z of a point behind the star (the planet is not between the star and
+ *     the observer) is PT_Z_BEHIND; its flux is 1.
+ *
+ * Readings of points the paper leaves open (repeated where they apply):
+ *   - t0 is the time of inferior conjunction (true anomaly pi/2 - w).
+ *   - Eccentric orbits: b = a cos i (1 - e^2)/(1 + e sin w) (Winn 2010).
+ *   - Supersamples sit at t + t_exp ((s + 1/2)/n_ss - 1/2); the point value
+ *     is their unweighted mean (Sec. 3.2, "n evenly distributed subsamples").
+ *   - Gimenez: G_j(p,q;x) = 2F1(-j, p+j; q; x) and the series keeps
+ *     j = 0 .. n_j-1 (N_J terms, Sec. 2.1.1).
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque CUDA stream (binary-compatible with cudaStream_t). */
+typedef struct CUstream_st *pt_stream_t;
+
+enum {
+    PT_OK = 0,
+    PT_ERR_ARG = 1,           /* null pointer, negative size or inconsistent sizes */
+    PT_ERR_DOMAIN = 2,        /* parameter outside the supported domain */
+    PT_ERR_NOT_CONVERGED = 3, /* reserved: reported through n_bad counters */
+    PT_ERR_CUDA = 4,          /* kernel launch or CUDA runtime error */
+    PT_ERR_WORKSPACE = 5      /* work buffer null or smaller than required */
+};
+
+#define PT_Z_BEHIND 1.0e30f
+
+/* Library version (major*10000 + minor*100 + patch). */
+int pt_version(void);
+
+/* Static text of a status code. */
+const char *pt_status_string(int status);
+
+/* Text of the last CUDA error seen by this host thread ("" if none). */
+const char *pt_last_error_string(void);
+
+/*
+ * Orbit parameters, structure of arrays; every array is a DEVICE pointer
+ * with n_v entries.
+ *   t0  : time of inferior conjunction [days]          (FP64)
+ *   P   : orbital period [days]                        (FP64)
+ *   a   : semi-major axis in stellar radii             (FP32)
+ *   inc : inclination [radians]                        (FP32)
+ *   e   : eccentricity in [0, 0.95], or NULL for circular orbits (values are not checked on the host)
+ *   w   : argument of periastron [radians]; NULL iff e is NULL
+ * Times are FP64 so that the phase of a point 10^3 days from t0 keeps
+ * sub-millisecond accuracy; everything after the phase reduction is FP32.
+ */
+typedef struct pt_orbit {
+    const double *t0;
+    const double *P;
+    const float *a;
+    const float *inc;
+    const float *e;
+    const float *w;
+    int n_v;
+} pt_orbit;
+
+/* ------------------------------------------------------------------------
+ * Projected separation z(t) (Sec. 1: "circular and elliptic orbits (using
+ * ... Newton's method ...)").  The paper gives no formula; the library uses
+ * z = r sqrt(cos^2(w+f) + sin^2(w+f) cos^2 i), r = a(1 - e cos E), with the
+ * true anomaly f from E and E from Kepler's equation E - e sin E = M.
+ *
+ * Output z_dev is [n_v][n_t * n_ss] (FP32): z of vector v at time index i and
+ * supersample s sits at z_dev[v*n_t*n_ss + i*n_ss + s].
+ * ---------------------------------------------------------------------- */
+
+/* Circular orbit: z = a sqrt(sin^2 phi + cos^2 i cos^2 phi), phi = 2 pi (t - t0)/P
+ * reduced in FP64; orb->e and orb->w are ignored. */
+int pt_z_circ(const double *t_dev, int n_t, const pt_orbit *orb, int n_ss, double t_exp,
+              float *z_dev, pt_stream_t stream);
+
+/* Eccentric orbit: FP64 Newton iteration on Kepler's equation per point
+ * (at most max_iter steps; converged when |dE| < tol), then z in FP32.
+ * Points that did not converge are counted into *n_bad_dev (device int,
+ * may be NULL; the caller zeroes it) and keep their last iterate. */
+int pt_z_ecc(const double *t_dev, int n_t, const pt_orbit *orb, int n_ss, double t_exp, int max_iter,
+             double tol, float *z_dev, int *n_bad_dev, pt_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Pointwise Mandel & Agol terms (Sec. 2.2.1, Eq. ma_model; the functions
+ * are those of Mandel & Agol 2002, Table 1).  For n pairs (k[i], z[i]):
+ *   lam_e[i]  = uniform-disk covered fraction lambda_e,
+ *   lam_d[i]  = lambda_d + 2/3 Theta(k - z)   (the Theta term folded in),
+ *   eta_d[i]  = eta_d,
+ * so that f = 1 - [(1-c) lam_e + c lam_d + u2 eta_d] / (1 - u1/3 - u2/6)
+ * with c = u1 + 2 u2.  All FP32 device arrays; k > 0.  Any output may be NULL.
+ * ---------------------------------------------------------------------- */
+int pt_ma_terms(const float *k_dev, const float *z_dev, size_t n, float *lam_e_dev, float *lam_d_dev,
+                float *eta_d_dev, pt_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Quadratic Mandel-Agol light curves (Sec. 2.2; supersampling Sec. 3.2;
+ * multiple passbands Sec. 2.2.2; device likelihood Sec. 3.4).
+ *
+ *   t_dev      [n_t] FP64 exposure mid-times (any order)
+ *   orb        orbit parameters of the n_v vectors (circular if orb->e NULL)
+ *   k_dev      radius ratios: [n_v] if k_per_band == 0, else [n_v][n_b]
+ *   ld_dev     [n_v][n_b][2] quadratic coefficients (u1, u2)
+ *   n_b        passbands per vector
+ *   n_ss       supersamples per exposure (>= 1); t_exp exposure time [days]
+ *   max_iter   cap on Newton steps for eccentric orbits, 1..64 (e.g. 16)
+ *   y_dev, wt_dev  [n_b][n_t] observed fluxes and weights (wt may be NULL
+ *              for unit weights); needed only when ssr_dev != NULL
+ *   flux_dev   [n_v][n_b][n_t] output flux cube, or NULL
+ *   ssr_dev    [n_v][n_b] output sum_t wt (y - f)^2, or NULL
+ *   work_dev   device scratch of at least pt_ma_quad_work_bytes() bytes
+ *   n_bad_dev  optional device int: points whose Newton iteration hit
+ *              max_iter are added to it
+ * With k_per_band == 0 one geometry pass serves all n_b limb-darkening sets
+ * (the factoring of Sec. 2.2.2); with k_per_band == 1 every passband has its
+ * own radius ratio and is evaluated as its own geometry.
+ * At least one of flux_dev and ssr_dev must be non-NULL.
+ * ---------------------------------------------------------------------- */
+size_t pt_ma_quad_work_bytes(int n_t, int n_v, int n_b, int k_per_band);
+
+int pt_ma_quad(const double *t_dev, int n_t, const pt_orbit *orb, const float *k_dev, int k_per_band,
+               const float *ld_dev, int n_b, int n_ss, double t_exp, int max_iter, const float *y_dev,
+               const float *wt_dev, float *flux_dev, float *ssr_dev, void *work_dev, size_t work_bytes,
+               int *n_bad_dev, pt_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Gimenez series light curves (Sec. 2.1).
+ *
+ * A plan holds the tables of Sec. 2.1.4 for a given number of general-law
+ * coefficients N (Eq. ld_general; alpha_0..alpha_N are evaluated) and series
+ * depth n_j: the recursion coefficients of G_j(nu+2, 1; x) and the A_{n,j}
+ * of Eq. (gimemez_a), in device memory allocated by pt_gim_plan_create and
+ * released by pt_gim_plan_destroy.  1 <= N <= 16, 2 <= n_j <= 512.
+ * A plan may be used from any stream; it is read-only after creation.
+ * ---------------------------------------------------------------------- */
+typedef struct pt_gim_plan_s *pt_gim_plan;
+
+int pt_gim_plan_create(int N, int n_j, pt_gim_plan *plan_out);
+int pt_gim_plan_destroy(pt_gim_plan plan);
+
+/* Pointwise alpha_n (Eq. gimenez): alpha_dev is [n][N+1] for n pairs (k, z). */
+int pt_gimenez_alpha(pt_gim_plan plan, const float *k_dev, const float *z_dev, size_t n,
+                     float *alpha_dev, pt_stream_t stream);
+
+/* Light curves: arguments as pt_ma_quad, with ld_dev [n_v][n_b][N] holding
+ * u_1..u_N of Eq. (ld_general) and f = 1 - sum_n C_n alpha_n (Sec. 2.1.3). */
+size_t pt_gimenez_work_bytes(pt_gim_plan plan, int n_t, int n_v, int n_b, int k_per_band);
+
+int pt_gimenez(pt_gim_plan plan, const double *t_dev, int n_t, const pt_orbit *orb, const float *k_dev,
+               int k_per_band, const float *ld_dev, int n_b, int n_ss, double t_exp, int max_iter,
+               const float *y_dev, const float *wt_dev, float *flux_dev, float *ssr_dev, void *work_dev,
+               size_t work_bytes, int *n_bad_dev, pt_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H */

@@ -1,1 +1,270 @@
-"""GB300-native transit-model hot path (placeholder; the CUDA binding follows)."""
+"""GB300 (sm_103a) transit-model hot path: thin Python binding of ``include/pt.h``.
+
+Every function here marshals arguments (torch CUDA tensors -> device
+pointers, the current CUDA stream) and calls the C ABI of
+``libpt_gb300.so``; all arithmetic runs in the library's CUDA kernels.  There
+is no CPU fallback: if the library is missing or no GPU is visible the calls
+raise.
+
+Model: Parviainen (2015), PyTransit -- quadratic Mandel-Agol (Sec. 2.2) and
+Gimenez (Sec. 2.1) transit fluxes over times x parameter vectors x passbands,
+with exposure supersampling (Sec. 3.2), circular/eccentric orbits (Sec. 1) and
+an optional on-device likelihood reduction (Sec. 3.4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build_mod
+
+__all__ = ["load_library", "Orbit", "orbit_to_device", "z_circ", "z_ecc", "ma_terms", "ma_quad",
+           "ma_quad_work_bytes", "GimenezPlan", "gimenez", "gimenez_alpha", "PTError", "Z_BEHIND"]
+
+Z_BEHIND = 1.0e30
+
+_c_void_p = ctypes.c_void_p
+_c_int = ctypes.c_int
+_c_size = ctypes.c_size_t
+_c_double = ctypes.c_double
+
+
+class PTError(RuntimeError):
+    pass
+
+
+class Orbit(ctypes.Structure):
+    """Mirror of ``pt_orbit`` (device pointers)."""
+    _fields_ = [("t0", _c_void_p), ("P", _c_void_p), ("a", _c_void_p), ("inc", _c_void_p),
+                ("e", _c_void_p), ("w", _c_void_p), ("n_v", _c_int)]
+
+
+_LIB = None
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libpt_gb300.so (raises if it is not built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build_mod.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build_mod.build()
+        else:
+            raise PTError("libpt_gb300.so is not built; run __graft_entry__.build() or "
+                          "python -m paper_1504_07433_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = _c_void_p
+    sig = {
+        "pt_version": (_c_int, []),
+        "pt_status_string": (ctypes.c_char_p, [_c_int]),
+        "pt_last_error_string": (ctypes.c_char_p, []),
+        "pt_z_circ": (_c_int, [P, _c_int, ctypes.POINTER(Orbit), _c_int, _c_double, P, P]),
+        "pt_z_ecc": (_c_int, [P, _c_int, ctypes.POINTER(Orbit), _c_int, _c_double, _c_int, _c_double, P, P, P]),
+        "pt_ma_terms": (_c_int, [P, P, _c_size, P, P, P, P]),
+        "pt_ma_quad_work_bytes": (_c_size, [_c_int, _c_int, _c_int, _c_int]),
+        "pt_ma_quad": (_c_int, [P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int, _c_double, _c_int,
+                                P, P, P, P, P, _c_size, P, P]),
+        "pt_gim_plan_create": (_c_int, [_c_int, _c_int, ctypes.POINTER(_c_void_p)]),
+        "pt_gim_plan_destroy": (_c_int, [P]),
+        "pt_gimenez_alpha": (_c_int, [P, P, P, _c_size, P, P]),
+        "pt_gimenez_work_bytes": (_c_size, [P, _c_int, _c_int, _c_int, _c_int]),
+        "pt_gimenez": (_c_int, [P, P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int, _c_double,
+                                _c_int, P, P, P, P, P, _c_size, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status, what):
+    if status != 0:
+        lib = load_library()
+        raise PTError("%s failed: %s (%s)" % (what, lib.pt_status_string(status).decode(),
+                                              lib.pt_last_error_string().decode()))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return _c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise PTError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise PTError("expected a contiguous tensor")
+    return _c_void_p(x.data_ptr())
+
+
+def _dev(x, dtype, device):
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(x, dtype=dtype, device=device).contiguous()
+
+
+def orbit_to_device(orbit, device="cuda"):
+    """Copy an orbit dict (t0, P, a, inc[, e, w]) to device tensors with the
+    ABI's dtypes (t0, P FP64; the rest FP32)."""
+    torch = _torch()
+    out = dict(t0=_dev(orbit["t0"], torch.float64, device), P=_dev(orbit["P"], torch.float64, device),
+               a=_dev(orbit["a"], torch.float32, device), inc=_dev(orbit["inc"], torch.float32, device))
+    if orbit.get("e") is not None:
+        out["e"] = _dev(orbit["e"], torch.float32, device)
+        out["w"] = _dev(orbit["w"], torch.float32, device)
+    else:
+        out["e"] = None
+        out["w"] = None
+    return out
+
+
+def _orbit_struct(orb):
+    n_v = int(orb["t0"].numel())
+    return Orbit(_ptr(orb["t0"]), _ptr(orb["P"]), _ptr(orb["a"]), _ptr(orb["inc"]),
+                 _ptr(orb.get("e")), _ptr(orb.get("w")), n_v), n_v
+
+
+def z_circ(t, orb, n_ss=1, t_exp=0.0):
+    """z[v, i*n_ss + s] for a circular orbit (pt_z_circ)."""
+    torch = _torch()
+    lib = load_library()
+    o, n_v = _orbit_struct(orb)
+    z = torch.empty((n_v, t.numel() * n_ss), dtype=torch.float32, device=t.device)
+    _check(lib.pt_z_circ(_ptr(t), t.numel(), ctypes.byref(o), n_ss, float(t_exp), _ptr(z), _stream()),
+           "pt_z_circ")
+    return z
+
+
+def z_ecc(t, orb, n_ss=1, t_exp=0.0, max_iter=50, tol=1e-12):
+    """z[v, i*n_ss + s] for an eccentric orbit with FP64 Newton (pt_z_ecc);
+    returns (z, n_bad) with n_bad a device int tensor."""
+    torch = _torch()
+    lib = load_library()
+    o, n_v = _orbit_struct(orb)
+    z = torch.empty((n_v, t.numel() * n_ss), dtype=torch.float32, device=t.device)
+    bad = torch.zeros(1, dtype=torch.int32, device=t.device)
+    _check(lib.pt_z_ecc(_ptr(t), t.numel(), ctypes.byref(o), n_ss, float(t_exp), int(max_iter), float(tol),
+                        _ptr(z), _ptr(bad), _stream()), "pt_z_ecc")
+    return z, bad
+
+
+def ma_terms(k, z):
+    """(lambda_e, lambda_d + 2/3 Theta(k-z), eta_d) for (k, z) pairs (pt_ma_terms)."""
+    torch = _torch()
+    lib = load_library()
+    k = k.contiguous()
+    z = z.contiguous()
+    le = torch.empty_like(z)
+    ld = torch.empty_like(z)
+    ed = torch.empty_like(z)
+    _check(lib.pt_ma_terms(_ptr(k), _ptr(z), z.numel(), _ptr(le), _ptr(ld), _ptr(ed), _stream()), "pt_ma_terms")
+    return le, ld, ed
+
+
+def ma_quad_work_bytes(n_t, n_v, n_b, k_per_band=False):
+    return int(load_library().pt_ma_quad_work_bytes(n_t, n_v, n_b, int(bool(k_per_band))))
+
+
+def _lc_outputs(n_v, n_b, n_t, want_flux, want_ssr, device, flux, ssr):
+    torch = _torch()
+    if want_flux and flux is None:
+        flux = torch.empty((n_v, n_b, n_t), dtype=torch.float32, device=device)
+    if want_ssr and ssr is None:
+        ssr = torch.empty((n_v, n_b), dtype=torch.float32, device=device)
+    return (flux if want_flux else None), (ssr if want_ssr else None)
+
+
+def ma_quad(t, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None, want_flux=True, want_ssr=False,
+            work=None, flux=None, ssr=None, n_bad=None):
+    """Quadratic Mandel-Agol light curves (pt_ma_quad).
+
+    t [n_t] float64; orb from orbit_to_device; k [n_v] or [n_v, n_b] float32;
+    ld [n_v, n_b, 2] float32 (u1, u2).  Returns (flux [n_v, n_b, n_t] or None,
+    ssr [n_v, n_b] or None)."""
+    torch = _torch()
+    lib = load_library()
+    o, n_v = _orbit_struct(orb)
+    n_b = int(ld.shape[1])
+    kpb = 1 if k.dim() == 2 else 0
+    n_t = t.numel()
+    fl, ss = _lc_outputs(n_v, n_b, n_t, want_flux, want_ssr, t.device, flux, ssr)
+    need = int(lib.pt_ma_quad_work_bytes(n_t, n_v, n_b, kpb))
+    if work is None or work.numel() < need:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=t.device)
+    _check(lib.pt_ma_quad(_ptr(t), n_t, ctypes.byref(o), _ptr(k), kpb, _ptr(ld), n_b, int(n_ss), float(t_exp),
+                          int(max_iter), _ptr(y), _ptr(wt), _ptr(fl), _ptr(ss), _ptr(work), work.numel(),
+                          _ptr(n_bad), _stream()), "pt_ma_quad")
+    return fl, ss
+
+
+class GimenezPlan:
+    """Tables of Sec. 2.1.4 (A_{n,j} and the Jacobi recursion) for N
+    general-law coefficients and series depth n_j (pt_gim_plan_create)."""
+
+    def __init__(self, N, n_j):
+        lib = load_library()
+        h = _c_void_p()
+        _check(lib.pt_gim_plan_create(int(N), int(n_j), ctypes.byref(h)), "pt_gim_plan_create")
+        self.handle = h
+        self.N = int(N)
+        self.n_j = int(n_j)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load_library().pt_gim_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def work_bytes(self, n_t, n_v, n_b, k_per_band=False):
+        return int(load_library().pt_gimenez_work_bytes(self.handle, n_t, n_v, n_b, int(bool(k_per_band))))
+
+
+def gimenez_alpha(plan, k, z):
+    """alpha_0..alpha_N for (k, z) pairs (pt_gimenez_alpha): [n, N+1]."""
+    torch = _torch()
+    lib = load_library()
+    k = k.contiguous()
+    z = z.contiguous()
+    out = torch.empty((z.numel(), plan.N + 1), dtype=torch.float32, device=z.device)
+    _check(lib.pt_gimenez_alpha(plan.handle, _ptr(k), _ptr(z), z.numel(), _ptr(out), _stream()),
+           "pt_gimenez_alpha")
+    return out
+
+
+def gimenez(plan, t, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None, want_flux=True,
+            want_ssr=False, work=None, flux=None, ssr=None, n_bad=None):
+    """Gimenez light curves (pt_gimenez); ld [n_v, n_b, N] holds u_1..u_N."""
+    torch = _torch()
+    lib = load_library()
+    o, n_v = _orbit_struct(orb)
+    n_b = int(ld.shape[1])
+    if int(ld.shape[2]) != plan.N:
+        raise PTError("ld has %d coefficients, plan expects %d" % (int(ld.shape[2]), plan.N))
+    kpb = 1 if k.dim() == 2 else 0
+    n_t = t.numel()
+    fl, ss = _lc_outputs(n_v, n_b, n_t, want_flux, want_ssr, t.device, flux, ssr)
+    need = plan.work_bytes(n_t, n_v, n_b, kpb)
+    if work is None or work.numel() < need:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=t.device)
+    _check(lib.pt_gimenez(plan.handle, _ptr(t), n_t, ctypes.byref(o), _ptr(k), kpb, _ptr(ld), n_b, int(n_ss),
+                          float(t_exp), int(max_iter), _ptr(y), _ptr(wt), _ptr(fl), _ptr(ss), _ptr(work),
+                          work.numel(), _ptr(n_bad), _stream()), "pt_gimenez")
+    return fl, ss

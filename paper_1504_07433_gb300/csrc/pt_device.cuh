@@ -1,0 +1,289 @@
+// pt_device.cuh -- device-side building blocks of the transit-model kernels.
+//
+// Everything here is FP32 except where a comment says otherwise.  The
+// numerical choices are documented next to the code; the formulas follow
+// Parviainen (2015) Sec. 2.2.1, Eq. (ma_model), with the lambda/eta functions
+// of Mandel & Agol (2002), which the paper defers to.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define PT_PI_F 3.14159265358979f
+#define PT_ZBEHIND 1.0e30f
+
+namespace pt {
+
+// ---------------------------------------------------------------------------
+// Per-geometry record, written by the set-up kernel and staged in shared
+// memory by the light-curve kernels.  One record per (vector) or, when every
+// passband has its own radius ratio, per (vector, passband).
+//
+// Time is reduced in double-float arithmetic: t0 and P are split into a
+// high float and the float of the remainder, so that t - t0 - n P keeps
+// ~1e-11 d absolute accuracy at |t| ~ 1e3 d without FP64 instructions on the
+// hot path.  The eccentric-orbit anchor (the eccentric anomaly at
+// conjunction) is computed in FP64 by the set-up kernel and enters the hot
+// path only multiplied by small quantities (see orbit_z below).
+// ---------------------------------------------------------------------------
+struct __align__(16) GeomRec {
+    float t0h, t0l, Ph, Pl;   // double-float t0 and P
+    float invP, nang;         // 1/P, 2 pi / P
+    float win_lo, win_hi;     // transit window in (t - t0 - nP) [days]; empty if lo > hi
+    float a, cosi, k, ecc;    // a/R*, cos i, radius ratio, 0 = circular / 1 = eccentric
+    float ecE, esE, cE, sE;   // e cos E_tr, e sin E_tr, cos E_tr, sin E_tr
+    float Uc, Us, Vs, Vc;     // a cos w, a sqrt(1-e^2) sin w, a sin w, a sqrt(1-e^2) cos w
+    float Vtr, pad0, pad1, pad2;  // r at conjunction = a (1 - e cos E_tr)
+};
+static_assert(sizeof(GeomRec) == 96, "GeomRec layout");
+
+// t - t0 - n P for the nearest epoch n, in double-float arithmetic.
+// (th, tl) is the double-float split of t.  Two-sum error terms are exact.
+__device__ __forceinline__ float reduce_time(float th, float tl, const GeomRec &r)
+{
+    float s = th - r.t0h;
+    float bv = s - th;
+    float e1 = (th - (s - bv)) + (-r.t0h - bv);
+    float n = rintf(s * r.invP);
+    float p = n * r.Ph;
+    float pe = fmaf(n, r.Ph, -p);          // n*Ph = p + pe exactly
+    float d = s - p;
+    float bv2 = d - s;
+    float e2 = (s - (d - bv2)) + (-p - bv2);
+    float lo = ((e1 + e2) - pe) + (tl - r.t0l) - n * r.Pl;
+    return d + lo;
+}
+
+// Projected separation z at time offset dt from conjunction (Sec. 1; the
+// paper prints no orbit formula).
+//   Circular:  phi = 2 pi dt / P,  z = a sqrt(sin^2 phi + cos^2 i cos^2 phi).
+//   Eccentric: Kepler's equation is solved relative to the conjunction
+//     anchor E_tr (M_tr = E_tr - e sin E_tr):
+//       dE - e cos E_tr sin dE + e sin E_tr (1 - cos dE) = dM,  dM = 2 pi dt / P,
+//     by Newton's method.  Position in the sky plane relative to conjunction:
+//       U = r cos(w + f) = a cos w dC - a sqrt(1-e^2) sin w dS        (U_tr = 0)
+//       V = r sin(w + f) = V_tr + a sin w dC + a sqrt(1-e^2) cos w dS
+//     with dC = cos E - cos E_tr, dS = sin E - sin E_tr formed from sin dE and
+//     1 - cos dE = 2 sin^2(dE/2).  Every term is small near transit, so FP32
+//     keeps relative accuracy there; z = sqrt(U^2 + V^2 cos^2 i).
+//   Behind the star (cos phi <= 0, or V <= 0) returns PT_ZBEHIND.
+// *bad is set when Newton did not converge within max_iter steps.
+__device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_iter, bool *bad)
+{
+    if (r.ecc == 0.0f) {
+        float s, c;
+        sincosf(r.nang * dt, &s, &c);
+        if (c <= 0.0f) return PT_ZBEHIND;
+        float ci = r.cosi * c;
+        return r.a * sqrtf(fmaf(s, s, ci * ci));
+    }
+    float dM = r.nang * dt;
+    float dE = dM / (1.0f - r.ecE);
+    float sh, ch;
+    bool conv = false;
+    for (int it = 0; it < max_iter; ++it) {
+        sincosf(0.5f * dE, &sh, &ch);
+        float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
+        float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
+        float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
+        float step = F / Fp;
+        dE -= step;
+        if (fabsf(step) <= 4e-7f * fabsf(dE) + 1e-12f) {
+            conv = true;
+            break;
+        }
+    }
+    if (!conv) *bad = true;
+    sincosf(0.5f * dE, &sh, &ch);
+    float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
+    float dC = -r.cE * omc - r.sE * sn;
+    float dS = r.cE * sn - r.sE * omc;
+    float U = r.Uc * dC - r.Us * dS;
+    float V = r.Vtr + (r.Vs * dC + r.Vc * dS);
+    if (V <= 0.0f) return PT_ZBEHIND;
+    float Vi = V * r.cosi;
+    return sqrtf(fmaf(U, U, Vi * Vi));
+}
+
+// ---------------------------------------------------------------------------
+// Bulirsch's general complete elliptic integral (Bulirsch 1969, Numer. Math.
+// 13, 305),
+//   cel(kc, p, a, b) = int_0^{pi/2} (a cos^2 + b sin^2) /
+//                      ((cos^2 + p sin^2) sqrt(cos^2 + kc^2 sin^2)) dth,
+// evaluated for two (p, a, b) triples that share kc: the Gauss/Landen
+// sequence of (kc, m) does not depend on (p, a, b), so the two integrals
+// share its square roots.  The first triple has p = 1 (the K/E combination
+// a K + (b - a) ... is folded into (a, b) by the caller), the second has
+// p = rho > 0 and b = 0.  Converged when the arithmetic-geometric means agree
+// to 3e-4 (quadratic convergence then leaves ~1e-7); at most 10 steps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cel2(float kc, float a1, float b1, float rho, float a2, float *r1,
+                                     float *r2)
+{
+    float p1 = 1.0f;
+    float p2 = sqrtf(rho);
+    float b2 = 0.0f;
+    float m = 1.0f, e = kc;
+#pragma unroll 1
+    for (int it = 0; it < 10; ++it) {
+        float ip1 = __fdividef(1.0f, p1);
+        float ip2 = __fdividef(1.0f, p2);
+        float f = a1;
+        a1 = fmaf(b1, ip1, a1);
+        float g = e * ip1;
+        b1 = 2.0f * fmaf(f, g, b1);
+        p1 += g;
+        f = a2;
+        a2 = fmaf(b2, ip2, a2);
+        g = e * ip2;
+        b2 = 2.0f * fmaf(f, g, b2);
+        p2 += g;
+        g = m;
+        m = kc + m;
+        if (fabsf(g - kc) <= g * 3e-4f) break;
+        kc = 2.0f * sqrtf(e);
+        e = kc * m;
+    }
+    *r1 = (0.5f * PT_PI_F) * fmaf(a1, m, b1) / (m * (m + p1));
+    *r2 = (0.5f * PT_PI_F) * fmaf(a2, m, b2) / (m * (m + p2));
+}
+
+// ---------------------------------------------------------------------------
+// Mandel & Agol (2002) terms for the quadratic law, FP32.
+//   le = lambda_e, ld = lambda_d + 2/3 Theta(p - z), ed = eta_d.
+//
+// Geometry: d = z + p - 1, 1 - a = (1 - z + p)(1 + z - p), b - 1 = d (1 + z + p),
+// q = (p - z)(p + z); all formed from single differences so they keep
+// relative precision at the contact points.  kap0, kap1 and the triangle
+// area come from atan2 of the Heron area (no acos of a rounded cosine).
+//
+// lambda_1 (partial) and lambda_2 (inside) are Mandel & Agol's
+//   pref {cK K(k) + cE E(k) + cP Pi(n, k)}.
+// Near z = 1 - p the modulus tends to 1 and K, Pi diverge logarithmically
+// while their divergences cancel.  The kernel removes the cancellation
+// algebraically:  with rho = 1 - n,
+//   cP Pi = (cP/rho) K + cP (rho - 1)/rho * cel(kc, rho, 1, 0),
+// and cK' = cK + cP/rho factors through b - 1:
+//   lambda_1: cK' = -(b-1)(6 p^2 + 2 p z - 3),              cR = -3 q (1-a)/a
+//   lambda_2: cK' = (b-1)(p^3 - p^2 z - p z^2 + 2p + z^3 - 4z)/(p+z),
+//             cR = -12 q z p / (a b)
+// so the brace is cel(kc, 1, cK'+cE, cK'+cE kc^2) + cel(kc, rho, cR, 0), two
+// bounded integrals evaluated in one shared loop (cel2).
+// Exact special cases of Mandel & Agol's Table 1 that the general formulas
+// cannot evaluate (z = 1 - p, z = p, p = z = 1/2, star covered) are taken
+// separately; near them the general formulas stay accurate in FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld, float *ed)
+{
+    *le = 0.0f;
+    *ld = 0.0f;
+    *ed = 0.0f;
+    if (!(z < 1.0f + p) || !(p > 0.0f)) return;    // out of transit (also PT_ZBEHIND, NaN)
+    if (p >= 1.0f && z <= p - 1.0f) {               // case 11: star covered
+        *le = 1.0f;
+        *ld = 2.0f / 3.0f;
+        *ed = 0.5f;
+        return;
+    }
+    const float pi = PT_PI_F;
+    float p2 = p * p, z2 = z * z;
+    float d = (z - 1.0f) + p;
+    float oma = (1.0f - z + p) * (1.0f + z - p);
+    float bm1 = d * (1.0f + z + p);
+    float zmp = z - p;
+    float a = zmp * zmp;
+    float b = (z + p) * (z + p);
+    float q = -zmp * (p + z);
+    float eta2 = 0.5f * p2 * (p2 + 2.0f * z2);
+    bool inside = d < 0.0f;
+
+    float fa = sqrtf(fmaxf(0.0f, oma * bm1));       // 4 x triangle area
+    float k1 = atan2f(fa, 1.0f - p2 + z2);
+    float k0 = atan2f(fa, p2 + z2 - 1.0f);
+    float le_part = (p2 * k0 + k1 - 0.5f * fa) * (1.0f / pi);
+    float eta1 = (k1 + 2.0f * eta2 * k0 - 0.25f * (1.0f + 5.0f * p2 + z2) * fa) * (0.5f / pi);
+
+    // parameters of the shared elliptic evaluation
+    float kc, cKp, cE, rho = 1.0f, cR = 0.0f, pref, cst = 0.0f;
+    bool need_cel = true;
+    float e_out = inside ? eta2 : eta1;
+    if (d == 0.0f) {                                 // case 4: lambda_5, z = 1 - p
+        cst = 2.0f / (3.0f * pi) * acosf(1.0f - 2.0f * p) -
+              4.0f / (9.0f * pi) * (3.0f + 2.0f * p - 8.0f * p2) * sqrtf(p * (1.0f - p)) -
+              (p > 0.5f ? 2.0f / 3.0f : 0.0f);
+        e_out = eta2;
+        need_cel = false;
+        kc = 1.0f; cKp = 0.0f; cE = 0.0f; pref = 0.0f;
+    } else if (zmp == 0.0f) {                        // z = p
+        if (p == 0.5f) {                             // case 6
+            cst = 1.0f / 3.0f - 4.0f / (9.0f * pi);
+            e_out = 3.0f / 32.0f;
+            need_cel = false;
+            kc = 1.0f; cKp = 0.0f; cE = 0.0f; pref = 0.0f;
+        } else if (p < 0.5f) {                       // case 5: lambda_4, modulus 2p
+            kc = sqrtf((1.0f - 2.0f * p) * (1.0f + 2.0f * p));
+            cKp = 1.0f - 4.0f * p2;
+            cE = 4.0f * (2.0f * p2 - 1.0f);
+            pref = 2.0f / (9.0f * pi);
+            cst = 1.0f / 3.0f;
+            e_out = eta2;
+        } else {                                     // case 7: lambda_3, modulus 1/(2p)
+            kc = sqrtf((2.0f * p - 1.0f) * (2.0f * p + 1.0f)) / (2.0f * p);
+            cKp = -(1.0f - 4.0f * p2) * (3.0f - 8.0f * p2) / p;
+            cE = 16.0f * p * (2.0f * p2 - 1.0f);
+            pref = 1.0f / (9.0f * pi);
+            cst = 1.0f / 3.0f;
+            e_out = eta1;
+        }
+    } else if (inside) {                             // cases 3, 9: lambda_2
+        kc = sqrtf(-bm1 / oma);
+        cKp = bm1 * (p2 * p - p2 * z - p * z2 + 2.0f * p + z2 * z - 4.0f * z) / (p + z);
+        cE = oma * (z2 + 7.0f * p2 - 4.0f);
+        rho = b / a;
+        cR = -12.0f * q * z * p / (a * b);
+        pref = 2.0f / (9.0f * pi * sqrtf(oma));
+    } else {                                         // cases 2, 8: lambda_1
+        kc = sqrtf(bm1 / (4.0f * z * p));
+        cKp = -bm1 * (6.0f * p2 + 2.0f * p * z - 3.0f);
+        cE = 4.0f * p * z * (z2 + 7.0f * p2 - 4.0f);
+        rho = 1.0f / a;
+        cR = -3.0f * q * oma / a;
+        pref = 1.0f / (9.0f * pi * sqrtf(p * z));
+    }
+    float lam = cst;
+    if (need_cel) {
+        float r1, r2;
+        cel2(kc, cKp + cE, fmaf(cE, kc * kc, cKp), rho, cR, &r1, &r2);
+        lam = fmaf(pref, r1 + r2, cst);
+    }
+    if (p > z) lam += 2.0f / 3.0f;
+    *le = inside ? p2 : le_part;
+    *ld = lam;
+    *ed = e_out;
+}
+
+// Quadratic-law weights of Eq. (ma_model): f = 1 - (we le + wd ld + wn ed),
+// with c = u1 + 2 u2 and the normalisation 1 - u1/3 - u2/6.
+__device__ __forceinline__ void ma_weights(float u1, float u2, float *we, float *wd, float *wn)
+{
+    float inv = 1.0f / (1.0f - u1 * (1.0f / 3.0f) - u2 * (1.0f / 6.0f));
+    float c = u1 + 2.0f * u2;
+    *we = (1.0f - c) * inv;
+    *wd = c * inv;
+    *wn = u2 * inv;
+}
+
+// Warp-aggregated append to a shared-memory queue; returns the slot.
+__device__ __forceinline__ int warp_append(int *counter, bool pred)
+{
+    unsigned mask = __ballot_sync(0xffffffffu, pred);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (mask != 0u && lane == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader < 0 ? 0 : leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+}  // namespace pt

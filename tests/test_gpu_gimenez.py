@@ -1,0 +1,127 @@
+"""GPU parity of the Gimenez path (pt_gimenez_alpha, pt_gimenez) against the
+FP64 oracle at the same series depth n_j, through the C ABI.
+
+Tolerance: 1e-6 absolute flux (the exact-path bound), alpha_n to 5e-7.
+The truncation error against the exact flux is a separate, reported
+property (Fig. 1 behaviour), checked here only as MA-Gimenez agreement.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_07433_gb300 import workloads as W
+from tests.helpers import f32, gpu_inputs, oracle_orbit
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1504_07433_gb300 as pt
+    pt.load_library()
+    return torch
+
+
+@pytest.mark.parametrize("n_j", [16, 64, 160])
+def test_gimenez_alpha_vs_oracle(torch_cuda, n_j):
+    torch = torch_cuda
+    import paper_1504_07433_gb300 as pt
+    plan = pt.GimenezPlan(8, n_j)
+    rng = np.random.default_rng(n_j)
+    k = rng.uniform(0.01, 0.3, 400).astype(np.float32)
+    z = (rng.uniform(0, 1.05, k.size) * (1 + k)).astype(np.float32)
+    z[:8] = 0.0
+    z[8:16] = (1 - k[8:16])
+    a = pt.gimenez_alpha(plan, torch.as_tensor(k, device="cuda"), torch.as_tensor(z, device="cuda")).cpu().numpy()
+    ref = np.array([oracle.gimenez_alpha(8, n_j, float(kk), float(zz)) for kk, zz in zip(k, z)])
+    assert np.max(np.abs(a - ref)) <= 5e-7
+    u = rng.uniform(-0.05, 0.3, (k.size, 8))
+    D = 1 - np.sum(np.arange(1, 9) * u / (np.arange(1, 9) + 2), axis=1)
+    C = np.concatenate([(1 - u.sum(1))[:, None], u], axis=1) / D[:, None]
+    assert np.max(np.abs(np.sum(C * (a - ref), axis=1))) <= TOL
+
+
+def _oracle_lc(wl, n_j):
+    return oracle.lc_gimenez(wl["t"], oracle_orbit(wl["orbit"]), f32(wl["k"]), f32(wl["ld_gim"]), n_j,
+                             n_ss=wl["n_ss"], t_exp=wl["t_exp"])[0]
+
+
+@pytest.mark.parametrize("n_t,n_v,n_ss,n_j", [(1500, 5, 10, 128), (700, 3, 1, 64), (301, 2, 3, 40)])
+def test_gimenez_lc_vs_oracle(torch_cuda, n_t, n_v, n_ss, n_j):
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=n_v, n_t=n_t, n_ss=n_ss, cadence=0.01)
+    wl["ld"] = wl["ld_gim"]
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(8, n_j)
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flux, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=n_ss, t_exp=wl["t_exp"], n_bad=bad)
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = _oracle_lc(wl, n_j)
+    assert int(bad.item()) == 0
+    assert (ref < 1).sum() > 0
+    assert np.max(np.abs(f - ref)) <= TOL
+
+
+def test_gimenez_ssr_and_multiband(torch_cuda):
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.batched(n_walkers=3, n_pb=4, n_lc=2, len_lo=200, len_hi=400)
+    rng = np.random.default_rng(2)
+    u = np.concatenate([W.quad_to_general(wl["ld"][..., 0], wl["ld"][..., 1], 2),
+                        rng.uniform(-0.02, 0.02, wl["ld"].shape[:2] + (2,))], axis=-1)
+    wl["ld"] = u
+    wl["k"] = wl["k"][:, 0]
+    plan = pt.GimenezPlan(4, 96)
+    t, orb, k, ld = gpu_inputs(wl)
+    y = torch.as_tensor(wl["y"], dtype=torch.float32, device="cuda")
+    flux, ssr = pt.gimenez(plan, t, orb, k, ld, y=y, want_ssr=True)
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = oracle.lc_gimenez(wl["t"], oracle_orbit(wl["orbit"]), f32(wl["k"]), f32(u), 96)[0]
+    assert np.max(np.abs(f - ref)) <= TOL
+    yy = np.asarray(wl["y"], np.float32).astype(np.float64)
+    assert np.allclose(ssr.cpu().numpy(), np.sum((yy[None] - f) ** 2, axis=2), rtol=2e-5)
+
+
+def test_gimenez_agrees_with_ma_for_quadratic_ld(torch_cuda):
+    """Same physics: with u_1 = a + 2b, u_2 = -b (Sec. 2.1.2) the two GPU
+    models agree to the series truncation error (n_j = 300 here)."""
+    import paper_1504_07433_gb300 as pt
+    wl = W.long_cadence(n_v=8, n_t=3000, n_ss=1, cadence=0.005)
+    t, orb, k, ld = gpu_inputs(wl)
+    fm, _ = pt.ma_quad(t, orb, k, ld)
+    import torch
+    ldg = torch.as_tensor(W.quad_to_general(wl["ld"][..., 0], wl["ld"][..., 1], 2), dtype=torch.float32,
+                          device="cuda")
+    fg, _ = pt.gimenez(pt.GimenezPlan(2, 300), t, orb, k, ldg)
+    assert torch.max(torch.abs(fm - fg)).item() < 5e-6
+
+
+def test_gimenez_full_long_cadence_sampled(torch_cuda):
+    """Full 50,000 x 256 x 10 workload with N = 8, n_j = 128 in the
+    benchmark's launch configuration; sampled outputs against the oracle."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence()
+    wl["ld"] = wl["ld_gim"]
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(8, 128)
+    flux, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+    f = flux.cpu().numpy()
+    assert np.all(f <= 1.0 + 1e-6) and np.all(f > 0.9)
+    rng = np.random.default_rng(22)
+    for v in rng.choice(256, 12, replace=False):
+        row = f[v, 0]
+        intr = np.nonzero(row < 1.0)[0]
+        pick = np.concatenate([rng.choice(intr, min(40, intr.size), replace=False),
+                               rng.choice(row.size, 10, replace=False)])
+        sub = dict(t=wl["t"][pick], orbit={kk: (None if vv is None else np.asarray(vv)[[v]])
+                                          for kk, vv in wl["orbit"].items()},
+                   k=wl["k"][[v]], ld_gim=wl["ld_gim"][[v]], n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+        ref = _oracle_lc(sub, 128)
+        assert np.max(np.abs(row[pick].astype(np.float64) - ref[0, 0])) <= TOL, v

@@ -1,0 +1,226 @@
+"""GPU parity of the Mandel-Agol path (pt_ma_terms, pt_z_circ, pt_z_ecc,
+pt_ma_quad) against the FP64 oracle, through the C ABI.
+
+Tolerance: 1e-6 absolute flux for the exact FP32 path (the bound the
+workload specification sets); z to 1e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_07433_gb300 import workloads as W
+from tests.helpers import f32, gpu_inputs, oracle_orbit
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1504_07433_gb300 as pt
+    pt.load_library()
+    return torch
+
+
+def _special_z(k):
+    k32 = np.float32(k)
+    pts = [0.0, k32, np.float32(1.0) - k32, np.float32(1.0) + k32]
+    near = []
+    for p in pts:
+        for d in (1e-7, 1e-6, 1e-5, 1e-4, 1e-3):
+            near += [p - d, p + d]
+    return np.array([x for x in pts + near if x >= 0], dtype=np.float32)
+
+
+KS = [0.01, 0.05, 0.1, 0.15, 0.2, 0.3, 0.45, 0.5, 0.6, 0.9, 1.2]
+
+
+@pytest.mark.parametrize("k", KS)
+def test_ma_terms_flux_vs_oracle(torch_cuda, k):
+    torch = torch_cuda
+    import paper_1504_07433_gb300 as pt
+    zs = np.concatenate([np.linspace(0.0, 1.0 + k + 0.05, 3001, dtype=np.float32), _special_z(k)])
+    kk = np.full_like(zs, np.float32(k))
+    le, ld, ed = pt.ma_terms(torch.as_tensor(kk, device="cuda"), torch.as_tensor(zs, device="cuda"))
+    le, ld, ed = (x.cpu().numpy().astype(np.float64) for x in (le, ld, ed))
+    kd = float(np.float32(k))
+    for u1, u2 in [(0.4, 0.2), (0.0, 0.0), (1.0, 0.0), (0.1, 0.7), (0.9, -0.2)]:
+        c = u1 + 2 * u2
+        D = 1 - u1 / 3 - u2 / 6
+        f_gpu = 1 - ((1 - c) * le + c * ld + u2 * ed) / D
+        f_ref = oracle.flux_quad_vec(kd, zs.astype(np.float64), u1, u2)
+        err = np.abs(f_gpu - f_ref)
+        i = int(np.argmax(err))
+        assert err[i] <= TOL, "k=%g u=(%g,%g) z=%.9g gpu=%.9g ref=%.9g" % (k, u1, u2, zs[i], f_gpu[i], f_ref[i])
+    out = zs >= np.float32(1.0) + np.float32(k)
+    assert np.all(le[out] == 0) and np.all(ld[out] == 0) and np.all(ed[out] == 0)
+
+
+def test_ma_terms_random_dense(torch_cuda):
+    torch = torch_cuda
+    import paper_1504_07433_gb300 as pt
+    rng = np.random.default_rng(11)
+    k = rng.uniform(0.01, 0.35, 20000).astype(np.float32)
+    z = (rng.uniform(0.0, 1.0, k.size) * (1.0 + k) * 1.02).astype(np.float32)
+    le, ld, ed = pt.ma_terms(torch.as_tensor(k, device="cuda"), torch.as_tensor(z, device="cuda"))
+    le, ld, ed = (x.cpu().numpy().astype(np.float64) for x in (le, ld, ed))
+    f_gpu = 1 - ((1 - 0.8) * le + 0.8 * ld + 0.2 * ed) / (1 - 0.4 / 3 - 0.2 / 6)
+    f_ref = oracle.flux_quad_vec(k.astype(np.float64), z.astype(np.float64), 0.4, 0.2)
+    assert np.max(np.abs(f_gpu - f_ref)) <= TOL
+
+
+def test_z_circ_vs_oracle(torch_cuda):
+    import paper_1504_07433_gb300 as pt
+    wl = W.plain()
+    wl["t"] = np.linspace(-2.0, 1000.0, 4099)
+    t, orb, _, _ = gpu_inputs(wl)
+    z = pt.z_circ(t, orb, n_ss=3, t_exp=0.02).cpu().numpy().astype(np.float64)
+    zr, _ = oracle.z_batch(wl["t"], oracle_orbit(wl["orbit"]), n_ss=3, t_exp=0.02)
+    front = zr < 1e29
+    assert np.array_equal(front, z < 1e29)
+    assert np.allclose(z[front], zr[front], rtol=1e-6, atol=1e-7)
+
+
+def test_z_ecc_fp64_newton_vs_oracle(torch_cuda):
+    import paper_1504_07433_gb300 as pt
+    wl = W.long_cadence(n_v=16, n_t=2000, n_ss=2)
+    t, orb, _, _ = gpu_inputs(wl)
+    z, bad = pt.z_ecc(t, orb, n_ss=2, t_exp=wl["t_exp"])
+    z = z.cpu().numpy().astype(np.float64)
+    zr, nbad = oracle.z_batch(wl["t"], oracle_orbit(wl["orbit"]), n_ss=2, t_exp=wl["t_exp"])
+    assert int(bad.item()) == 0 and nbad == 0
+    front = zr < 1e29
+    # points within 1e-9 of the behind/front boundary may land on either side
+    assert np.mean(front == (z < 1e29)) > 0.9999
+    both = front & (z < 1e29)
+    assert np.allclose(z[both], zr[both], rtol=1e-6, atol=1e-7)
+
+
+def _oracle_lc(wl, k=None, ld=None):
+    return oracle.lc_ma(wl["t"], oracle_orbit(wl["orbit"]), f32(wl["k"] if k is None else k),
+                        f32(wl["ld"] if ld is None else ld), n_ss=wl["n_ss"], t_exp=wl["t_exp"])[0]
+
+
+def test_ma_quad_plain(torch_cuda):
+    import paper_1504_07433_gb300 as pt
+    wl = W.plain()
+    t, orb, k, ld = gpu_inputs(wl)
+    flux, _ = pt.ma_quad(t, orb, k, ld)
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = _oracle_lc(wl)
+    assert np.max(np.abs(f - ref)) <= TOL
+    # symmetric about t0 for a circular orbit (the grid is symmetric)
+    assert np.max(np.abs(f[0, 0] - f[0, 0, ::-1])) <= 2 * TOL
+    assert f.min() < 0.99
+
+
+@pytest.mark.parametrize("n_t,n_v,n_ss,n_b", [(3001, 21, 10, 2), (257, 9, 3, 1), (1, 1, 1, 1), (255, 8, 7, 3)])
+def test_ma_quad_eccentric_supersampled(torch_cuda, n_t, n_v, n_ss, n_b):
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=n_v, n_t=n_t, n_ss=n_ss, cadence=0.013)
+    rng = np.random.default_rng(5)
+    ld = np.repeat(wl["ld"], n_b, axis=1)
+    ld[:, 1:, :] = rng.uniform(0.0, 0.4, (n_v, n_b - 1, 2)) if n_b > 1 else ld[:, 1:, :]
+    wl["ld"] = ld
+    t, orb, k, ldt = gpu_inputs(wl)
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flux, _ = pt.ma_quad(t, orb, k, ldt, n_ss=n_ss, t_exp=wl["t_exp"], n_bad=bad)
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = _oracle_lc(wl)
+    assert int(bad.item()) == 0
+    err = np.abs(f - ref)
+    assert err.max() <= TOL, np.unravel_index(np.argmax(err), err.shape)
+    if n_t > 100:
+        assert (ref < 1).sum() > 0
+
+
+def test_ma_quad_circular_multiband_factoring(torch_cuda):
+    """One geometry pass serves n_b limb-darkening sets (Sec. 2.2.2): every
+    passband equals a single-passband evaluation with its own LD pair."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.batched(n_walkers=6, n_pb=5, n_lc=3, len_lo=300, len_hi=900)
+    wl["k"] = wl["k"][:, 0]
+    t, orb, k, ld = gpu_inputs(wl)
+    flux, _ = pt.ma_quad(t, orb, k, ld)
+    ref = _oracle_lc(wl)
+    assert np.max(np.abs(flux.cpu().numpy() - ref)) <= TOL
+    for b in range(5):
+        fb, _ = pt.ma_quad(t, orb, k, ld[:, b:b + 1, :].contiguous())
+        assert torch.equal(fb[:, 0], flux[:, b])
+
+
+def test_ma_quad_k_per_band_and_ssr(torch_cuda):
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.batched(n_walkers=5, n_pb=7, n_lc=4, len_lo=200, len_hi=700)
+    rng = np.random.default_rng(9)
+    wt = rng.uniform(0.5, 2.0, wl["y"].shape)
+    t, orb, k, ld = gpu_inputs(wl)
+    y = torch.as_tensor(wl["y"], dtype=torch.float32, device="cuda")
+    wtt = torch.as_tensor(wt, dtype=torch.float32, device="cuda")
+    flux, ssr = pt.ma_quad(t, orb, k, ld, y=y, wt=wtt, want_ssr=True)
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = _oracle_lc(wl)
+    assert np.max(np.abs(f - ref)) <= TOL
+    # the device reduction against FP64 sums of the same residuals
+    yy = np.asarray(wl["y"], np.float32).astype(np.float64)
+    ww = np.asarray(wt, np.float32).astype(np.float64)
+    ssr_own = np.sum(ww[None] * (yy[None] - f) ** 2, axis=2)
+    s = ssr.cpu().numpy().astype(np.float64)
+    assert np.allclose(s, ssr_own, rtol=2e-5, atol=0)
+    # and against the oracle, within the bound the flux tolerance implies
+    ssr_ref = oracle.ssr(ref, yy, ww)
+    bound = np.sum(ww[None] * (2 * np.abs(yy[None] - ref) * TOL + TOL ** 2), axis=2) + 2e-5 * ssr_ref
+    assert np.all(np.abs(s - ssr_ref) <= bound)
+    # SSR-only call gives the same numbers
+    _, ssr2 = pt.ma_quad(t, orb, k, ld, y=y, wt=wtt, want_flux=False, want_ssr=True)
+    assert torch.equal(ssr, ssr2)
+
+
+def test_ma_quad_deterministic_and_empty(torch_cuda):
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=16, n_t=4000, n_ss=10)
+    t, orb, k, ld = gpu_inputs(wl)
+    f1, _ = pt.ma_quad(t, orb, k, ld, n_ss=10, t_exp=wl["t_exp"])
+    f2, _ = pt.ma_quad(t, orb, k, ld, n_ss=10, t_exp=wl["t_exp"])
+    assert torch.equal(f1, f2)
+    # zero times: a no-op that returns PT_OK
+    t0 = t[:0]
+    f0, _ = pt.ma_quad(t0, orb, k, ld)
+    assert f0.shape == (16, 1, 0)
+
+
+def test_ma_quad_full_long_cadence_sampled(torch_cuda):
+    """The full 50,000 x 256 x 10 workload in the benchmark's launch
+    configuration, checked on sampled outputs the oracle computes one by one,
+    plus properties that hold at any size."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence()
+    t, orb, k, ld = gpu_inputs(wl)
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flux, _ = pt.ma_quad(t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], n_bad=bad)
+    f = flux.cpu().numpy()
+    assert int(bad.item()) == 0
+    assert np.all(f <= 1.0) and np.all(f > 0.9)
+    rng = np.random.default_rng(21)
+    vs = rng.choice(256, 48, replace=False)
+    for v in vs:
+        row = f[v, 0]
+        intr = np.nonzero(row < 1.0)[0]
+        pick = np.concatenate([rng.choice(intr, min(120, intr.size), replace=False),
+                               rng.choice(row.size, 40, replace=False)])
+        sub = dict(t=wl["t"][pick], orbit={kk: (None if vv is None else np.asarray(vv)[[v]])
+                                          for kk, vv in wl["orbit"].items()},
+                   k=wl["k"][[v]], ld=wl["ld"][[v]], n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+        ref = _oracle_lc(sub)
+        assert np.max(np.abs(row[pick].astype(np.float64) - ref[0, 0])) <= TOL, v
