@@ -861,9 +861,10 @@ static int lc_common_check(const double *t, int n_t, const pt_orbit *orb, const 
     if (n_t < 0 || n_b < 1 || n_ss < 1 || n_ss > MAX_SS || max_iter < 1 || max_iter > MAX_NEWTON)
         return PT_ERR_ARG;
     if (k_per_band != 0 && k_per_band != 1) return PT_ERR_ARG;
+    if (n_t == 0 || orb->n_v == 0) return PT_OK;   // nothing to evaluate
     if (!flux && !ssr) return PT_ERR_ARG;
-    if (n_t > 0 && orb->n_v > 0 && (!t || !k || !ld)) return PT_ERR_ARG;
-    if (ssr && n_t > 0 && !y) return PT_ERR_ARG;
+    if (!t || !k || !ld) return PT_ERR_ARG;
+    if (ssr && !y) return PT_ERR_ARG;
     if (!work) return PT_ERR_WORKSPACE;
     return PT_OK;
 }

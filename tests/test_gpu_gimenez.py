@@ -40,7 +40,11 @@ def test_gimenez_alpha_vs_oracle(torch_cuda, n_j):
     a = pt.gimenez_alpha(plan, torch.as_tensor(k, device="cuda"), torch.as_tensor(z, device="cuda")).cpu().numpy()
     ref = np.array([oracle.gimenez_alpha(8, n_j, float(kk), float(zz)) for kk, zz in zip(k, z)])
     assert np.max(np.abs(a - ref)) <= 5e-7
-    u = rng.uniform(-0.05, 0.3, (k.size, 8))
+    # physical 8-term laws: a quadratic law in general form plus small higher terms
+    q1, q2 = rng.uniform(0, 1, k.size), rng.uniform(0, 1, k.size)
+    u = np.zeros((k.size, 8))
+    u[:, :2] = W.quad_to_general(*W.q_to_u(q1, q2), 2)
+    u[:, 2:] = rng.uniform(-0.02, 0.02, (k.size, 6))
     D = 1 - np.sum(np.arange(1, 9) * u / (np.arange(1, 9) + 2), axis=1)
     C = np.concatenate([(1 - u.sum(1))[:, None], u], axis=1) / D[:, None]
     assert np.max(np.abs(np.sum(C * (a - ref), axis=1))) <= TOL
