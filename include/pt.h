@@ -154,6 +154,34 @@ int pt_ma_quad(const double *t_dev, int n_t, const pt_orbit *orb, const float *k
                int *n_bad_dev, pt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * pt_ma_quad without a work buffer.  The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory -- e.g. a host
+ * program whose device memory is all owned by its own fixed pool, or a tight
+ * sampling loop that must not stall on an allocation.  Arguments and results
+ * are those of pt_ma_quad minus work_dev/work_bytes; the caller still owns
+ * every input and output.
+ *
+ * Scratch comes from a static device array of PT_MA_NOALLOC_SCRATCH_BYTES
+ * (4 MiB) that every GPU loading the library keeps until the process exits.
+ * A problem whose pt_ma_quad_work_bytes() exceeds it is rejected with
+ * PT_ERR_WORKSPACE (see pt_last_error_string()) -- roughly n_t <= 400,000 for
+ * a few hundred vectors, less with SSR output over many rows.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The call allocates and frees nothing.
+ * All calls share the one array and it keeps the last call's contents;
+ * each call writes every scratch byte it reads, so nothing needs clearing,
+ * but calls that overlap on the GPU (different streams or threads) race on
+ * it and must be serialised by the caller.
+ * ---------------------------------------------------------------------- */
+#define PT_MA_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+int pt_ma_quad_noalloc(const double *t_dev, int n_t, const pt_orbit *orb, const float *k_dev, int k_per_band,
+                       const float *ld_dev, int n_b, int n_ss, double t_exp, int max_iter, const float *y_dev,
+                       const float *wt_dev, float *flux_dev, float *ssr_dev, int *n_bad_dev,
+                       pt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Gimenez series light curves (Sec. 2.1).
  *
  * A plan holds the tables of Sec. 2.1.4 for a given number of general-law

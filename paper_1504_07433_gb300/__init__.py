@@ -268,3 +268,26 @@ def gimenez(plan, t, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None
                           float(t_exp), int(max_iter), _ptr(y), _ptr(wt), _ptr(fl), _ptr(ss), _ptr(work),
                           work.numel(), _ptr(n_bad), _stream()), "pt_gimenez")
     return fl, ss
+
+
+def ma_quad_noalloc(t, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None, want_flux=True,
+                    want_ssr=False, flux=None, ssr=None, n_bad=None):
+    """pt_ma_quad_noalloc: pt_ma_quad with the library's static device scratch
+    instead of a work buffer, for callers that cannot allocate device memory
+    (the outputs are still the caller's; pass flux/ssr to avoid allocating
+    them here).  Rejects problems whose scratch exceeds
+    PT_MA_NOALLOC_SCRATCH_BYTES; overlapping calls on the GPU race."""
+    lib = load_library()
+    fn = lib.pt_ma_quad_noalloc
+    fn.restype = _c_int
+    P = _c_void_p
+    fn.argtypes = [P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int, _c_double, _c_int,
+                   P, P, P, P, P, P]
+    o, n_v = _orbit_struct(orb)
+    n_b = int(ld.shape[1])
+    kpb = 1 if k.dim() == 2 else 0
+    n_t = t.numel()
+    fl, ss = _lc_outputs(n_v, n_b, n_t, want_flux, want_ssr, t.device, flux, ssr)
+    _check(fn(_ptr(t), n_t, ctypes.byref(o), _ptr(k), kpb, _ptr(ld), n_b, int(n_ss), float(t_exp), int(max_iter),
+              _ptr(y), _ptr(wt), _ptr(fl), _ptr(ss), _ptr(n_bad), _stream()), "pt_ma_quad_noalloc")
+    return fl, ss

@@ -22,6 +22,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "../../include/pt.h"
 #include "pt_device.cuh"
 
@@ -1104,3 +1106,71 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free variant of pt_ma_quad.
+//
+// Some callers cannot call cudaMalloc: a host program that hands all device
+// memory to its own fixed pool and forbids outside allocations, or a tight
+// sampling loop where an allocation (and the stall it can cause) is not
+// acceptable.  For them pt_ma_quad_noalloc takes its scratch from a
+// statically sized __device__ array instead of a caller-provided work
+// buffer.  The array is part of the module image: every GPU that loads the
+// library holds PT_MA_NOALLOC_SCRATCH_BYTES of it until the process exits.
+// ===========================================================================
+namespace {
+
+static __device__ __align__(256) unsigned char g_ma_noalloc_scratch[PT_MA_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array for the current device.  In host code
+// the symbol name is only a host-side stand-in, so the address is fetched
+// with cudaGetSymbolAddress once per device (with that device current) and
+// cached.
+int noalloc_scratch(void **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_cuda_error(e, "pt_ma_quad_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        snprintf(g_last_error, sizeof(g_last_error), "pt_ma_quad_noalloc: device %d beyond the %d supported", dev,
+                 NOALLOC_MAX_DEVICES);
+        return PT_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_ma_noalloc_scratch);
+        if (e != cudaSuccess) return set_cuda_error(e, "pt_ma_quad_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PT_OK;
+}
+
+}  // namespace
+
+extern "C" int pt_ma_quad_noalloc(const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band,
+                                  const float *ld, int n_b, int n_ss, double t_exp, int max_iter,
+                                  const float *y, const float *wt, float *flux, float *ssr, int *n_bad,
+                                  pt_stream_t stream)
+{
+    if (!orb || n_t < 0 || orb->n_v < 0 || n_b < 1) return PT_ERR_ARG;
+    size_t need = pt_ma_quad_work_bytes(n_t, orb->n_v, n_b, k_per_band);
+    if (need > (size_t)PT_MA_NOALLOC_SCRATCH_BYTES) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "pt_ma_quad_noalloc: this problem needs %zu bytes of scratch, the static scratch holds %zu; "
+                 "use pt_ma_quad with a work buffer", need, (size_t)PT_MA_NOALLOC_SCRATCH_BYTES);
+        return PT_ERR_WORKSPACE;
+    }
+    void *scratch = nullptr;
+    int st = noalloc_scratch(&scratch);
+    if (st) return st;
+    // Every scratch byte the kernels read is written earlier in the same call
+    // (geometry records, time split, residual partials), so nothing is cleared.
+    return pt_ma_quad(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux, ssr, scratch,
+                      (size_t)PT_MA_NOALLOC_SCRATCH_BYTES, n_bad, stream);
+}
