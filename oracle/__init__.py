@@ -78,6 +78,10 @@ def _lib():
                                         _I, _I, _D, _PD, _I]),
                 ("pto_ssr", None, [_PD, _PD, _PD, _I, _I, _I, _PD]),
                 ("pto_max_threads", _I, []),
+                ("pto_overlap_derivs", None, [_D, _D, _PD]),
+                ("pto_flux_theta", _D, [_D, _PD, _I, _D]),
+                ("pto_flux_grad", _D, [_D, _PD, _I, _D, _PD]),
+                ("pto_ssr_grad", None, [_PD, _I, _PD, _I, _I, _D, _PD, _PD, _PD, _PD, _I]),
             ]:
                 fn = getattr(lib, name)
                 fn.restype = res
@@ -259,3 +263,40 @@ def ssr(flux, y, wt=None):
 
 def max_threads():
     return _lib().pto_max_threads()
+
+
+# ---------------------------------------------------------------- gradients
+THETA = ("t0", "P", "a", "b", "e", "w", "k", "u1", "u2")
+
+
+def overlap_derivs(p, z):
+    """(dI1/dp, dI1/dz, dImu/dp, dImu/dz, dImu2/dp, dImu2/dz) of the overlap integrals."""
+    out = np.zeros(6)
+    _lib().pto_overlap_derivs(p, z, _ptr(out))
+    return out
+
+
+def flux_theta(t, th, n_ss=1, t_exp=0.0):
+    th = _arr(th, 9)
+    return _lib().pto_flux_theta(t, _ptr(th), n_ss, t_exp)
+
+
+def flux_grad(t, th, n_ss=1, t_exp=0.0):
+    th = _arr(th, 9)
+    g = np.zeros(9)
+    f = _lib().pto_flux_grad(t, _ptr(th), n_ss, t_exp, _ptr(g))
+    return f, g
+
+
+def ssr_grad(t, th, y, wt=None, n_ss=1, t_exp=0.0, n_threads=0):
+    """SSR [n_v] and d SSR / d theta [n_v, 9] for theta rows (t0, P, a, b, e, w, k, u1, u2)."""
+    t = _arr(t)
+    th = np.ascontiguousarray(np.asarray(th, dtype=np.float64).reshape(-1, 9))
+    y = _arr(y, t.size)
+    wt = None if wt is None else _arr(wt, t.size)
+    n_v = th.shape[0]
+    ssr = np.zeros(n_v)
+    grad = np.zeros((n_v, 9))
+    _lib().pto_ssr_grad(_ptr(t), t.size, _ptr(th), n_v, n_ss, t_exp, _ptr(y), _ptr(wt), _ptr(ssr), _ptr(grad),
+                        n_threads)
+    return ssr, grad

@@ -531,3 +531,189 @@ int pto_max_threads(void)
     return 1;
 #endif
 }
+
+
+/* ------------------------------------------------------------------------
+ * Gradients (the adjoint's reference).  The paper evaluates no gradients; it
+ * cites analytic derivatives of the quadratic model (Pal 2008).  Here they
+ * follow from the definition of the occulted flux:
+ *   I_g(p, z) = int int_{overlap} g(r) dA,  g in {1, mu, mu^2},  mu = sqrt(1 - r^2),
+ *   pi lambda_e = I_1,  pi (lambda_d + 2/3 Theta(p - z)) = I_mu,  pi eta_d = I_1 - I_mu2,
+ *   F = 1 - [(1 - u1 - u2) I_1 + (u1 + 2 u2) I_mu - u2 I_mu2] / (pi (1 - u1/3 - u2/6)).
+ * Only the planet's edge inside the star moves with p or z (Reynolds
+ * transport): with the edge point (z + p cos phi, p sin phi),
+ *   dI_g/dp = p int_arc g dphi,   dI_g/dz = p int_arc g cos(phi) dphi,
+ * where the arc is the full circle inside the star, or the part of it within
+ * kap0 of the direction towards the star centre.  For g = mu the arc
+ * integrals are complete elliptic integrals (with m1 = (1-a)/(4zp) on the
+ * partial arc, m2 = 4zp/(1-a) on the full circle, a = (z-p)^2).
+ * ---------------------------------------------------------------------- */
+
+/* S(m) = int_0^{pi/2} sin^2 cos^2 / sqrt(1 - m sin^2) dth: binomial series of
+ * (1 - m s^2)^(-1/2) term by term below m = 1/2 (60 terms, < 1e-20), and
+ * ((2-m) E - 2 (1-m) K) / (3 m^2) above, where that difference has no
+ * cancellation to speak of. */
+static double s2c2_int(double m)
+{
+    if (m < 0.5) {
+        double w[64];   /* w_j = int_0^{pi/2} sin^(2j) = (pi/2) C(2j,j)/4^j */
+        w[0] = 0.5 * PTO_PI;
+        for (int j = 1; j < 64; ++j) w[j] = w[j - 1] * (2.0 * j - 1.0) / (2.0 * j);
+        double c = 1.0, mn = 1.0, s = 0.0;   /* c_n = C(2n,n)/4^n */
+        for (int n = 0; n < 60; ++n) {
+            s += c * mn * (w[n + 1] - w[n + 2]);
+            c *= (2.0 * n + 1.0) / (2.0 * n + 2.0);
+            mn *= m;
+        }
+        return s;
+    }
+    double mc = 1.0 - m;
+    return ((2.0 - m) * pto_elle(m, mc) - 2.0 * mc * pto_ellk(mc)) / (3.0 * m * m);
+}
+
+/* d[0..5] = dI_1/dp, dI_1/dz, dI_mu/dp, dI_mu/dz, dI_mu2/dp, dI_mu2/dz. */
+void pto_overlap_derivs(double p, double z, double *d)
+{
+    for (int i = 0; i < 6; ++i) d[i] = 0.0;
+    z = fabs(z);
+    if (p <= 0.0 || z >= 1.0 + p) return;
+    if (p >= 1.0 && z <= p - 1.0) return;        /* star covered: nothing moves */
+    double a = (z - p) * (z - p);
+    double oma = (1.0 - z + p) * (1.0 + z - p);
+    double dd = (z - 1.0) + p;
+    double al = 1.0 - z * z - p * p;              /* mu^2 = al + 2 z p cos(psi) on the edge */
+    if (dd < 0.0) {                               /* full circle inside the star */
+        double m = 4.0 * z * p / oma;
+        d[0] = 2.0 * PTO_PI * p;
+        d[1] = 0.0;
+        d[2] = 4.0 * p * sqrt(oma) * pto_elle(m, 1.0 - m);
+        d[3] = -p * 4.0 * sqrt(oma) * m * s2c2_int(m);
+        d[4] = p * al * 2.0 * PTO_PI;
+        d[5] = -p * 2.0 * z * p * PTO_PI;
+        return;
+    }
+    double fa = sqrt(fmax(0.0, oma * dd * (1.0 + z + p)));
+    double kap0 = atan2(fa, p * p + z * z - 1.0);
+    double sk = fa / (2.0 * p * z), ck = (p * p + z * z - 1.0) / (2.0 * p * z);
+    double m1 = oma / (4.0 * z * p), mc1 = dd * (1.0 + z + p) / (4.0 * z * p);
+    double K = pto_ellk(mc1), E = pto_elle(m1, mc1);
+    double icos = -2.0 * sk, icos2 = kap0 + sk * ck;   /* arc integrals of cos, cos^2 */
+    d[0] = 2.0 * p * kap0;
+    d[1] = p * icos;
+    d[2] = 8.0 * p * sqrt(z * p) * (E - mc1 * K);
+    d[3] = -p * (4.0 / 3.0) * sqrt(4.0 * z * p) * ((2.0 * m1 - 1.0) * E + mc1 * K);
+    d[4] = p * (al * 2.0 * kap0 - 2.0 * z * p * icos);
+    d[5] = p * (al * icos - 2.0 * z * p * icos2);
+}
+
+/* Flux at time t for theta = (t0, P, a, b, e, w, k, u1, u2): the plain
+ * composition of the orbit (inclination from b) and Eq. (ma_model),
+ * supersampled.  Used as the function the gradient is checked against. */
+double pto_flux_theta(double t, const double *th, int n_ss, double t_exp)
+{
+    double inc = pto_inc_from_b(th[3], th[2], th[4], th[5]);
+    double f = 0.0;
+    for (int s = 0; s < n_ss; ++s) {
+        double tt = t + t_exp * ((s + 0.5) / n_ss - 0.5);
+        int st;
+        double z = pto_z_ecc(tt, th[0], th[1], th[2], inc, th[4], th[5], 60, 1e-15, &st);
+        f += pto_flux_quad(th[6], z, th[7], th[8]);
+    }
+    return f / n_ss;
+}
+
+/* Flux and its gradient with respect to theta at one time (chain rule
+ * through z, Kepler's equation and the conjunction anchor), FP64. */
+double pto_flux_grad(double t, const double *th, int n_ss, double t_exp, double *g)
+{
+    const double t0 = th[0], P = th[1], A = th[2], b = th[3], e = th[4], w = th[5];
+    const double k = th[6], u1 = th[7], u2 = th[8];
+    for (int i = 0; i < 9; ++i) g[i] = 0.0;
+    double se = sqrt(1.0 - e * e);
+    double sw = sin(w), cw = cos(w);
+    double ci = b * (1.0 + e * sw) / (A * (1.0 - e * e));          /* cos i */
+    double dci[9] = {0};
+    dci[2] = -ci / A;
+    dci[3] = (1.0 + e * sw) / (A * (1.0 - e * e));
+    dci[4] = b / A * (sw * (1.0 - e * e) + 2.0 * e * (1.0 + e * sw)) / ((1.0 - e * e) * (1.0 - e * e));
+    dci[5] = b / A * e * cw / (1.0 - e * e);
+    /* conjunction anchor and its derivatives: f_tr = pi/2 - w */
+    double ftr = 0.5 * PTO_PI - w;
+    double Etr = 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * ftr), sqrt(1.0 + e) * cos(0.5 * ftr));
+    double Mtr = Etr - e * sin(Etr);
+    double ecEt = 1.0 - e * cos(Etr);
+    double dMtr_dw = -ecEt * ecEt / se;                            /* -dM/df at f_tr */
+    double dMtr_de = -ecEt * sin(Etr) / (1.0 - e * e) - sin(Etr);  /* dM/de at fixed f */
+    double c0 = 1.0 - u1 - u2, c2 = u1 + 2.0 * u2, D = 1.0 - u1 / 3.0 - u2 / 6.0;
+    double fsum = 0.0;
+    for (int s = 0; s < n_ss; ++s) {
+        double tt = t + t_exp * ((s + 0.5) / n_ss - 0.5);
+        double x = (tt - t0) / P;
+        double M = Mtr + 2.0 * PTO_PI * (x - rint(x));
+        double E;
+        pto_kepler_newton(M, e, 60, 1e-15, &E);
+        double sE = sin(E), cE = cos(E);
+        double X = A * (cE - e), Y = A * se * sE;
+        double U = X * cw - Y * sw, V = X * sw + Y * cw;
+        if (V <= 0.0) { fsum += 1.0; continue; }
+        double z = sqrt(U * U + V * V * ci * ci);
+        double I[3], T[3], dI[6];
+        pto_ma_terms(k, z, T);
+        if (T[0] == 0.0 && T[1] == 0.0 && T[2] == 0.0) { fsum += 1.0; continue; }
+        I[0] = PTO_PI * T[0];
+        I[1] = PTO_PI * (T[1] + ((k > z) ? 2.0 / 3.0 : 0.0));
+        I[2] = PTO_PI * (T[0] - T[2]);
+        double N = c0 * I[0] + c2 * I[1] - u2 * I[2];
+        fsum += 1.0 - N / (PTO_PI * D);
+        pto_overlap_derivs(k, z, dI);
+        double dFdk = -(c0 * dI[0] + c2 * dI[2] - u2 * dI[4]) / (PTO_PI * D);
+        double dFdz = -(c0 * dI[1] + c2 * dI[3] - u2 * dI[5]) / (PTO_PI * D);
+        /* dM/dtheta, then dE = (dM + sin E de) / (1 - e cos E) */
+        double dM[9] = {0}, de[9] = {0}, da[9] = {0}, dw[9] = {0};
+        dM[0] = -2.0 * PTO_PI / P;
+        dM[1] = -2.0 * PTO_PI * (tt - t0) / (P * P);
+        dM[4] = dMtr_de;
+        dM[5] = dMtr_dw;
+        de[4] = 1.0;
+        da[2] = 1.0;
+        dw[5] = 1.0;
+        double gz[9];
+        for (int i = 0; i < 6; ++i) {
+            double dE = (dM[i] + sE * de[i]) / (1.0 - e * cE);
+            double dX = da[i] * (cE - e) - A * sE * dE - A * de[i];
+            double dY = da[i] * se * sE + A * se * cE * dE - A * e * sE / se * de[i];
+            double dU = dX * cw - dY * sw - V * dw[i];
+            double dV = dX * sw + dY * cw + U * dw[i];
+            gz[i] = (U * dU + V * ci * ci * dV + V * V * ci * dci[i]) / z;
+        }
+        for (int i = 0; i < 6; ++i) g[i] += dFdz * gz[i];
+        g[6] += dFdk;
+        g[7] += -((I[1] - I[0]) / (PTO_PI * D) + N / (3.0 * PTO_PI * D * D));
+        g[8] += -((-I[0] + 2.0 * I[1] - I[2]) / (PTO_PI * D) + N / (6.0 * PTO_PI * D * D));
+    }
+    for (int i = 0; i < 9; ++i) g[i] /= n_ss;
+    return fsum / n_ss;
+}
+
+/* SSR = sum_t wt (y - f)^2 and its gradient for n_v parameter vectors
+ * (th is [n_v][9]); y, wt are [n_t] (wt NULL: unit weights). */
+void pto_ssr_grad(const double *t, int n_t, const double *th, int n_v, int n_ss, double t_exp,
+                  const double *y, const double *wt, double *ssr, double *grad, int n_threads)
+{
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int v = 0; v < n_v; ++v) {
+        double s = 0.0, G[9] = {0}, g[9];
+        for (int i = 0; i < n_t; ++i) {
+            double f = pto_flux_grad(t[i], th + (size_t)v * 9, n_ss, t_exp, g);
+            double wi = wt ? wt[i] : 1.0;
+            double r = f - y[i];
+            s += wi * r * r;
+            for (int j = 0; j < 9; ++j) G[j] += 2.0 * wi * r * g[j];
+        }
+        ssr[v] = s;
+        for (int j = 0; j < 9; ++j) grad[(size_t)v * 9 + j] = G[j];
+    }
+}
