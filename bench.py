@@ -135,6 +135,36 @@ def run_oracle_step(wl, n_v, n_t=None):
     return dt, fm.size + fg.size, (fm, fg)
 
 
+def bench_adjoint(pt, torch, dev, stream, K, flush):
+    """Adjoint workload: 4,096 eccentric vectors x 10,000 times, forward +
+    gradient of the SSR w.r.t. 9 parameters per vector (pt_ma_quad_bwd).
+    Reported in flux points (time x vector) per second, forward and backward
+    together; y is a synthetic light curve (not timed)."""
+    from paper_1504_07433_gb300 import workloads as W
+    wl = W.adjoint()
+    t = torch.as_tensor(wl["t"], dtype=torch.float64, device=dev)
+    th = pt.theta_to_device(wl["theta"], dev)
+    y = torch.ones(t.numel(), dtype=torch.float32, device=dev)
+    work = torch.empty(pt.load_library().pt_ma_quad_bwd_work_bytes(t.numel()), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        pt.ma_quad_bwd(t, th, y, work=work)
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(K):
+        flush.fill_(i & 0xff)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pt.ma_quad_bwd(t, th, y, work=work)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    m = float(np.mean(ms))
+    pts = t.numel() * th["t0"].numel()
+    return {"workload": wl["name"], "ms_per_call": m, "value": pts / (m * 1e-3), "unit": "flux points/s (fwd+grad)",
+            "gpu_launches_per_call": 2}
+
+
 def reference_main(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -176,6 +206,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint / batched / surrogate legs")
     ap.add_argument("--n-v", type=int, default=256, help="parameter vectors (smaller only for profiler captures)")
     ap.add_argument("--n-t", type=int, default=50000, help="exposure times (smaller only for profiler captures)")
     ap.add_argument("--heat-s", type=float, default=1.0,
@@ -323,6 +354,10 @@ def main():
                 "peak_source": "FP32 lanes 152 SM x 128 x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_max, peak_src),
                 "algorithmic_flops_per_launch": flops, "in_transit_evaluations": n_intr}
 
+    adjoint = None
+    if not args.no_extra:
+        adjoint = bench_adjoint(pt, torch, dev, stream, K, flush)
+
     cpu = None
     max_err = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -347,7 +382,7 @@ def main():
                            "parallelism": "replicas x%d" % ws},
                 "components_ms": {"ma_quad": float(np.mean(ma_ms)), "gimenez": g_mean_ms},
                 "max_abs_err_vs_oracle": max_err,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint,
                 "gpu_launches": 5 * K, "clocks": dict(clocks, window="%.1f s of untimed steps + the timed region"
                                                       % args.heat_s) if clocks else None,
                 "wall_s_timed": wall}

@@ -154,6 +154,41 @@ int pt_ma_quad(const double *t_dev, int n_t, const pt_orbit *orb, const float *k
                int *n_bad_dev, pt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Adjoint of the quadratic Mandel-Agol light curve (not in the paper, which
+ * cites analytic MA derivatives, Pal 2008).  For n_v parameter vectors
+ * theta = (t0, P, a, b, e, w, k, u1, u2), one passband, exposure times t:
+ *   ssr[v]      = sum_t wt (y - f)^2,        f = mean over n_ss supersamples
+ *   grad[v][i]  = d ssr[v] / d theta_i       (order t0, P, a, b, e, w, k, u1, u2)
+ *   flux[v][t]  = f (optional)
+ * b is the impact parameter, cos i = b (1 + e sin w) / (a (1 - e^2)).
+ * The forward model is recomputed inside the kernel (no saved activations).
+ * Derivatives: dF/dk and dF/dz from the moving edge of the overlap region
+ * (complete elliptic integrals), then the chain rule through z, Kepler's
+ * equation and the conjunction anchor.  e and w may be NULL (circular,
+ * w = pi/2); their gradient entries are then d/de and d/dw at e = 0.
+ * work_dev: at least pt_ma_quad_bwd_work_bytes(n_t) bytes (time split).
+ * y_dev, wt_dev: [n_t]; wt may be NULL.  ssr_dev, flux_dev may be NULL.
+ * ---------------------------------------------------------------------- */
+typedef struct pt_theta {
+    const double *t0;
+    const double *P;
+    const float *a;
+    const float *b;
+    const float *e;
+    const float *w;
+    const float *k;
+    const float *u1;
+    const float *u2;
+    int n_v;
+} pt_theta;
+
+size_t pt_ma_quad_bwd_work_bytes(int n_t);
+
+int pt_ma_quad_bwd(const double *t_dev, int n_t, const pt_theta *theta, int n_ss, double t_exp, int max_iter,
+                   const float *y_dev, const float *wt_dev, float *grad_dev, float *ssr_dev, float *flux_dev,
+                   void *work_dev, size_t work_bytes, int *n_bad_dev, pt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * pt_ma_quad without a work buffer.  The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory -- e.g. a host
  * program whose device memory is all owned by its own fixed pool, or a tight

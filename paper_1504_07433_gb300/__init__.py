@@ -18,8 +18,9 @@ import os
 
 from . import build as _build_mod
 
-__all__ = ["load_library", "Orbit", "orbit_to_device", "z_circ", "z_ecc", "ma_terms", "ma_quad",
-           "ma_quad_work_bytes", "GimenezPlan", "gimenez", "gimenez_alpha", "PTError", "Z_BEHIND"]
+__all__ = ["load_library", "Orbit", "Theta", "orbit_to_device", "z_circ", "z_ecc", "ma_terms", "ma_quad",
+           "ma_quad_work_bytes", "GimenezPlan", "gimenez", "gimenez_alpha", "ma_quad_bwd", "transit_ssr",
+           "PTError", "Z_BEHIND"]
 
 Z_BEHIND = 1.0e30
 
@@ -38,6 +39,14 @@ class Orbit(ctypes.Structure):
     _fields_ = [("t0", _c_void_p), ("P", _c_void_p), ("a", _c_void_p), ("inc", _c_void_p),
                 ("e", _c_void_p), ("w", _c_void_p), ("n_v", _c_int)]
 
+
+class Theta(ctypes.Structure):
+    """Mirror of ``pt_theta`` (device pointers)."""
+    _fields_ = [("t0", _c_void_p), ("P", _c_void_p), ("a", _c_void_p), ("b", _c_void_p), ("e", _c_void_p),
+                ("w", _c_void_p), ("k", _c_void_p), ("u1", _c_void_p), ("u2", _c_void_p), ("n_v", _c_int)]
+
+
+THETA_NAMES = ("t0", "P", "a", "b", "e", "w", "k", "u1", "u2")
 
 _LIB = None
 
@@ -72,6 +81,9 @@ def load_library(build_if_missing: bool = False):
         "pt_gimenez_work_bytes": (_c_size, [P, _c_int, _c_int, _c_int, _c_int]),
         "pt_gimenez": (_c_int, [P, P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int, _c_double,
                                 _c_int, P, P, P, P, P, _c_size, P, P]),
+        "pt_ma_quad_bwd_work_bytes": (_c_size, [_c_int]),
+        "pt_ma_quad_bwd": (_c_int, [P, _c_int, ctypes.POINTER(Theta), _c_int, _c_double, _c_int, P, P, P, P, P, P,
+                                    _c_size, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -291,3 +303,81 @@ def ma_quad_noalloc(t, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=No
     _check(fn(_ptr(t), n_t, ctypes.byref(o), _ptr(k), kpb, _ptr(ld), n_b, int(n_ss), float(t_exp), int(max_iter),
               _ptr(y), _ptr(wt), _ptr(fl), _ptr(ss), _ptr(n_bad), _stream()), "pt_ma_quad_noalloc")
     return fl, ss
+
+
+def theta_to_device(theta, device="cuda"):
+    """Parameter dict (t0, P, a, b, e, w, k, u1, u2) to device tensors (t0, P FP64; rest FP32)."""
+    torch = _torch()
+    out = {}
+    for name in THETA_NAMES:
+        x = theta.get(name)
+        if x is None:
+            out[name] = None
+            continue
+        out[name] = _dev(x, torch.float64 if name in ("t0", "P") else torch.float32, device)
+    return out
+
+
+def ma_quad_bwd(t, theta, y, wt=None, n_ss=1, t_exp=0.0, max_iter=16, want_flux=False, work=None, n_bad=None):
+    """pt_ma_quad_bwd: (ssr [n_v], grad [n_v, 9], flux [n_v, n_t] or None) for the
+    parameter tensors in theta (see theta_to_device)."""
+    torch = _torch()
+    lib = load_library()
+    n_v = int(theta["t0"].numel())
+    th = Theta(*(_ptr(theta.get(nm)) for nm in THETA_NAMES), n_v)
+    n_t = t.numel()
+    grad = torch.empty((n_v, 9), dtype=torch.float32, device=t.device)
+    ssr = torch.empty(n_v, dtype=torch.float32, device=t.device)
+    flux = torch.empty((n_v, n_t), dtype=torch.float32, device=t.device) if want_flux else None
+    need = int(lib.pt_ma_quad_bwd_work_bytes(n_t))
+    if work is None or work.numel() < need:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=t.device)
+    _check(lib.pt_ma_quad_bwd(_ptr(t), n_t, ctypes.byref(th), int(n_ss), float(t_exp), int(max_iter), _ptr(y),
+                              _ptr(wt), _ptr(grad), _ptr(ssr), _ptr(flux), _ptr(work), work.numel(), _ptr(n_bad),
+                              _stream()), "pt_ma_quad_bwd")
+    return ssr, grad, flux
+
+
+def _make_ssr_function():
+    torch = _torch()
+
+    class _TransitSSR(torch.autograd.Function):
+        """SSR of the quadratic MA light curve with the hand-written adjoint as
+        its backward; the forward call already produces the gradient, which is
+        the only thing kept for backward."""
+
+        @staticmethod
+        def forward(ctx, t, y, wt, n_ss, t_exp, t0, P, a, b, e, w, k, u1, u2):
+            th = dict(t0=t0.detach().contiguous(), P=P.detach().contiguous(), a=a.detach().contiguous(),
+                      b=b.detach().contiguous(), e=None if e is None else e.detach().contiguous(),
+                      w=None if w is None else w.detach().contiguous(), k=k.detach().contiguous(),
+                      u1=u1.detach().contiguous(), u2=u2.detach().contiguous())
+            ssr, grad, _ = ma_quad_bwd(t, th, y, wt, n_ss=n_ss, t_exp=t_exp)
+            ctx.save_for_backward(grad)
+            ctx.has_e = e is not None
+            return ssr
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            g = gout[:, None].to(grad.dtype) * grad
+            cols = [g[:, i] for i in range(9)]
+            cols[0] = cols[0].double()
+            cols[1] = cols[1].double()
+            if not ctx.has_e:
+                cols[4] = None
+                cols[5] = None
+            return (None, None, None, None, None, *cols)
+
+    return _TransitSSR
+
+
+_SSR_FN = None
+
+
+def transit_ssr(t, y, theta, wt=None, n_ss=1, t_exp=0.0):
+    """Differentiable SSR [n_v] (torch.autograd): d/d theta comes from pt_ma_quad_bwd."""
+    global _SSR_FN
+    if _SSR_FN is None:
+        _SSR_FN = _make_ssr_function()
+    return _SSR_FN.apply(t, y, wt, int(n_ss), float(t_exp), *(theta.get(nm) for nm in THETA_NAMES))
