@@ -165,6 +165,56 @@ def bench_adjoint(pt, torch, dev, stream, K, flush):
             "gpu_launches_per_call": 2}
 
 
+def bench_batched(pt, torch, dev, stream, K, flush):
+    """Batched spectrophotometry: 1,024 walkers x 64 passbands (own k and LD)
+    x 32 light curves of 500-5,000 points, one graph-captured persistent
+    launch per evaluation, autotuned.  Two modes: fused SSR (no flux cube)
+    and the full FP32 flux cube (~23 GB written per evaluation)."""
+    from paper_1504_07433_gb300 import workloads as W
+    wl = W.batched()
+    t = torch.as_tensor(wl["t"], dtype=torch.float64, device=dev)
+    orb = pt.orbit_to_device(wl["orbit"], dev)
+    k = torch.as_tensor(wl["k"], dtype=torch.float32, device=dev)
+    ld = torch.as_tensor(wl["ld"], dtype=torch.float32, device=dev)
+    y = torch.as_tensor(wl["y"], dtype=torch.float32, device=dev)
+    n_v, n_b, n_t = k.shape[0], k.shape[1], t.numel()
+    pts = n_v * n_b * n_t
+    out = {"workload": wl["name"], "flux_points_per_call": pts}
+
+    def timed(plan):
+        for _ in range(2):
+            plan.run()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(K):
+            flush.fill_(i & 0xff)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms))
+
+    plan = pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, y=y, want_flux=False, want_ssr=True, autotune=True)
+    m = timed(plan)
+    out["ssr_mode"] = dict(plan.info(), ms_per_call=m, value=pts / (m * 1e-3), unit="flux points/s")
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
+    plan = pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, want_flux=True, want_ssr=False, autotune=True)
+    m = timed(plan)
+    peaks, src = _peaks()
+    gbs = 4.0 * pts / (m * 1e-3) / 1e9
+    out["cube_mode"] = dict(plan.info(), ms_per_call=m, value=pts / (m * 1e-3), unit="flux points/s",
+                            store_gbs=gbs, store_frac_of_hbm=gbs / float(peaks.get("hbm_gbs", 6800.0)))
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
+    return out
+
+
 def reference_main(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -354,9 +404,10 @@ def main():
                 "peak_source": "FP32 lanes 152 SM x 128 x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_max, peak_src),
                 "algorithmic_flops_per_launch": flops, "in_transit_evaluations": n_intr}
 
-    adjoint = None
+    adjoint = batched = None
     if not args.no_extra:
         adjoint = bench_adjoint(pt, torch, dev, stream, K, flush)
+        batched = bench_batched(pt, torch, dev, stream, K, flush)
 
     cpu = None
     max_err = None
@@ -383,6 +434,7 @@ def main():
                 "components_ms": {"ma_quad": float(np.mean(ma_ms)), "gimenez": g_mean_ms},
                 "max_abs_err_vs_oracle": max_err,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint,
+                "batched": batched,
                 "gpu_launches": 5 * K, "clocks": dict(clocks, window="%.1f s of untimed steps + the timed region"
                                                       % args.heat_s) if clocks else None,
                 "wall_s_timed": wall}

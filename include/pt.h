@@ -189,6 +189,50 @@ int pt_ma_quad_bwd(const double *t_dev, int n_t, const pt_theta *theta, int n_ss
                    void *work_dev, size_t work_bytes, int *n_bad_dev, pt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Batched evaluation for spectrophotometric MCMC (the paper's motivation,
+ * Sec. 1; per-passband limb darkening and radius ratio, Secs. 2.2.2 and 3.5;
+ * likelihood on the device, Sec. 3.4): n_v walkers x n_b passbands over
+ * n_lc light curves of uneven length, concatenated in t.  Every passband has
+ * its own k and (u1, u2); the orbit is per walker.
+ *
+ * pt_batch_plan_create() binds the buffers named in the descriptor (their
+ * addresses, not their contents), builds a work list of (walker, time tile)
+ * items that never straddle a light curve, times candidate configurations
+ * (tile length 64/128/256 x CTAs per SM) on those buffers when autotune is
+ * non-zero, and captures the chosen evaluation -- work-counter reset,
+ * per-walker set-up, one persistent kernel, residual reduction -- into a
+ * CUDA graph.  pt_batch_run() replays that graph on a stream: update the
+ * contents of the bound buffers (new walker parameters, new data) between
+ * runs.  The plan allocates its own work list and scratch (device memory)
+ * at creation and releases them in pt_batch_plan_destroy().
+ * ---------------------------------------------------------------------- */
+typedef struct pt_batch_desc {
+    const double *t;        /* [n_t] device, concatenated exposure times */
+    int n_t;
+    const int *lc_offsets;  /* [n_lc + 1] HOST: light curve j is t[lc_offsets[j] .. lc_offsets[j+1]) */
+    int n_lc;
+    pt_orbit orb;           /* n_v walkers (device arrays) */
+    const float *k;         /* [n_v][n_b] device */
+    const float *ld;        /* [n_v][n_b][2] device, (u1, u2) */
+    int n_b;                /* 1..256 */
+    int n_ss;               /* supersamples, 1..256 */
+    double t_exp;
+    int max_iter;           /* Newton cap for eccentric orbits, 1..64 */
+    const float *y;         /* [n_b][n_t] device, needed with ssr */
+    const float *wt;        /* [n_b][n_t] device or NULL */
+    float *flux;            /* [n_v][n_b][n_t] device or NULL */
+    float *ssr;             /* [n_v][n_b] device or NULL (not both NULL) */
+    int *n_bad;             /* optional device counter of non-converged Newton solves */
+} pt_batch_desc;
+
+typedef struct pt_batch_plan_s *pt_batch_plan;
+
+int pt_batch_plan_create(const pt_batch_desc *desc, int autotune, pt_batch_plan *plan_out);
+int pt_batch_run(pt_batch_plan plan, pt_stream_t stream);
+int pt_batch_plan_info(pt_batch_plan plan, int *tile, int *ctas_per_sm, int *n_items, float *tuned_ms);
+int pt_batch_plan_destroy(pt_batch_plan plan);
+
+/* ------------------------------------------------------------------------
  * pt_ma_quad without a work buffer.  The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory -- e.g. a host
  * program whose device memory is all owned by its own fixed pool, or a tight

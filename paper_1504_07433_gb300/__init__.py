@@ -381,3 +381,73 @@ def transit_ssr(t, y, theta, wt=None, n_ss=1, t_exp=0.0):
     if _SSR_FN is None:
         _SSR_FN = _make_ssr_function()
     return _SSR_FN.apply(t, y, wt, int(n_ss), float(t_exp), *(theta.get(nm) for nm in THETA_NAMES))
+
+
+class BatchDesc(ctypes.Structure):
+    """Mirror of ``pt_batch_desc``."""
+    _fields_ = [("t", _c_void_p), ("n_t", _c_int), ("lc_offsets", ctypes.POINTER(_c_int)), ("n_lc", _c_int),
+                ("orb", Orbit), ("k", _c_void_p), ("ld", _c_void_p), ("n_b", _c_int), ("n_ss", _c_int),
+                ("t_exp", _c_double), ("max_iter", _c_int), ("y", _c_void_p), ("wt", _c_void_p),
+                ("flux", _c_void_p), ("ssr", _c_void_p), ("n_bad", _c_void_p)]
+
+
+class BatchPlan:
+    """Persistent, graph-captured evaluation of n_v walkers x n_b passbands
+    over light curves of uneven length (pt_batch_plan_create / pt_batch_run).
+
+    The plan binds the given tensors (their storage, not their values):
+    update walker parameters or data in place between run() calls.
+    k [n_v, n_b], ld [n_v, n_b, 2], y/wt [n_b, n_t]; flux/ssr are outputs
+    ([n_v, n_b, n_t] / [n_v, n_b]); pass want_flux / want_ssr to allocate them.
+    """
+
+    def __init__(self, t, lc_offsets, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None,
+                 want_flux=True, want_ssr=False, autotune=True, n_bad=None):
+        torch = _torch()
+        lib = load_library()
+        for name, res, args in [("pt_batch_plan_create", _c_int, [ctypes.POINTER(BatchDesc), _c_int,
+                                                                 ctypes.POINTER(_c_void_p)]),
+                                ("pt_batch_run", _c_int, [_c_void_p, _c_void_p]),
+                                ("pt_batch_plan_info", _c_int, [_c_void_p, ctypes.POINTER(_c_int),
+                                                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                                                ctypes.POINTER(ctypes.c_float)]),
+                                ("pt_batch_plan_destroy", _c_int, [_c_void_p])]:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        o, n_v = _orbit_struct(orb)
+        n_b = int(k.shape[1])
+        n_t = t.numel()
+        self.flux = torch.empty((n_v, n_b, n_t), dtype=torch.float32, device=t.device) if want_flux else None
+        self.ssr = torch.empty((n_v, n_b), dtype=torch.float32, device=t.device) if want_ssr else None
+        offs = [int(x) for x in lc_offsets]
+        self._offs = (_c_int * len(offs))(*offs)
+        self._keep = (t, orb, k, ld, y, wt, n_bad)
+        d = BatchDesc(_ptr(t), n_t, self._offs, len(offs) - 1, o, _ptr(k), _ptr(ld), n_b, int(n_ss), float(t_exp),
+                      int(max_iter), _ptr(y), _ptr(wt), _ptr(self.flux), _ptr(self.ssr), _ptr(n_bad))
+        h = _c_void_p()
+        _check(lib.pt_batch_plan_create(ctypes.byref(d), int(bool(autotune)), ctypes.byref(h)),
+               "pt_batch_plan_create")
+        self.handle = h
+
+    def run(self):
+        _check(load_library().pt_batch_run(self.handle, _stream()), "pt_batch_run")
+        return self.flux, self.ssr
+
+    def info(self):
+        tile, cps, items = _c_int(), _c_int(), _c_int()
+        ms = ctypes.c_float()
+        load_library().pt_batch_plan_info(self.handle, ctypes.byref(tile), ctypes.byref(cps), ctypes.byref(items),
+                                          ctypes.byref(ms))
+        return dict(tile=tile.value, ctas_per_sm=cps.value, items=items.value, tuned_ms=ms.value)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().pt_batch_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,6 +22,10 @@
 #include "../../include/pt.h"
 #include "pt_device.cuh"
 
+namespace pt_internal {
+int set_error(int status, const char *where, const char *msg);   // pt_lc.cu
+}
+
 namespace {
 
 constexpr int TB = 256;
@@ -437,7 +441,7 @@ int pt_ma_quad_bwd(const double *t, int n_t, const pt_theta *th, int n_ss, doubl
     float2 *ts = (float2 *)work;
     tsplit_kernel<<<(n_t + 255) / 256, 256, 0, s>>>(t, n_t, ts);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return PT_ERR_CUDA;
+    if (e != cudaSuccess) return pt_internal::set_error(PT_ERR_CUDA, "tsplit_kernel", cudaGetErrorString(e));
     BwdArgs A;
     A.tsplit = ts;
     A.n_t = n_t;
@@ -453,7 +457,7 @@ int pt_ma_quad_bwd(const double *t, int n_t, const pt_theta *th, int n_ss, doubl
     A.n_bad = n_bad;
     ma_bwd_kernel<<<th->n_v, TB, 0, s>>>(A);
     e = cudaGetLastError();
-    return e == cudaSuccess ? PT_OK : PT_ERR_CUDA;
+    return e == cudaSuccess ? PT_OK : pt_internal::set_error(PT_ERR_CUDA, "ma_bwd_kernel", cudaGetErrorString(e));
 }
 
 }  // extern "C"

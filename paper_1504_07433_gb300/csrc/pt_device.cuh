@@ -274,6 +274,111 @@ __device__ __forceinline__ void ma_weights(float u1, float u2, float *we, float 
     *wn = u2 * inv;
 }
 
+constexpr double PT_PI_D = 3.14159265358979323846;
+
+__device__ __forceinline__ float wrap_pos(float x)   // into [0, 2 pi); closed form, no loop
+{
+    const float tp = 6.28318530717958f;
+    float y = x - tp * floorf(x / tp);
+    return (y >= tp) ? 0.0f : y;
+}
+
+__device__ __forceinline__ float wrap_neg(float x)   // into (-2 pi, 0]
+{
+    const float tp = 6.28318530717958f;
+    float y = wrap_pos(x);
+    return (y > 0.0f) ? y - tp : 0.0f;
+}
+
+// Per-geometry record (see GeomRec): double-float t0/P, the conjunction
+// anchor of an eccentric orbit (FP64 here; it enters the hot path only as
+// coefficients of small terms), sky-plane position coefficients, and a
+// conservative transit window in time for radius ratio k, widened by half
+// an exposure.
+__device__ __forceinline__ void make_geom_rec(double t0, double P, float a_f, float inc, bool ecc, float e_f,
+                                              float w_f, float k, float half_exp, GeomRec *out)
+{
+    GeomRec r;
+    r.t0h = (float)t0;
+    r.t0l = (float)(t0 - (double)r.t0h);
+    r.Ph = (float)P;
+    r.Pl = (float)(P - (double)r.Ph);
+    r.invP = (float)(1.0 / P);
+    r.nang = (float)(2.0 * PT_PI_D / P);
+    double a = a_f;
+    double ci = cos((double)inc);
+    r.a = (float)a;
+    r.cosi = (float)ci;
+    r.k = k;
+    double e = 0.0, w = 0.5 * PT_PI_D;
+    if (ecc) {
+        e = e_f;
+        w = w_f;
+    }
+    r.ecc = ecc ? 1.0f : 0.0f;
+    // conjunction anchor (FP64): f_tr = pi/2 - w, E_tr from tan(E/2) = sqrt((1-e)/(1+e)) tan(f/2)
+    double ftr = 0.5 * PT_PI_D - w;
+    double Etr = 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * ftr), sqrt(1.0 + e) * cos(0.5 * ftr));
+    double sE = sin(Etr), cE = cos(Etr);
+    double sw = sin(w), cw = cos(w), se = sqrt(1.0 - e * e);
+    r.ecE = (float)(e * cE);
+    r.esE = (float)(e * sE);
+    r.cE = (float)cE;
+    r.sE = (float)sE;
+    r.Uc = (float)(a * cw);
+    r.Us = (float)(a * se * sw);
+    r.Vs = (float)(a * sw);
+    r.Vc = (float)(a * se * cw);
+    r.Vtr = (float)(a * (1.0 - e * cE));
+    r.pad0 = r.pad1 = r.pad2 = 0.0f;
+    // Conservative window.  z^2 >= r_min^2 (sin^2(th) sin^2 i + cos^2 i) with
+    // th = w + f - pi/2 and r_min = a (1 - e), so z > 1 + k whenever
+    // sin^2 th > ((1+k)^2 / r_min^2 - cos^2 i) / sin^2 i.  The true-anomaly
+    // window [f_tr - th_w, f_tr + th_w] maps to a mean-anomaly window and
+    // from there to time; widened by half an exposure and a margin.
+    float rr = (1.0f + fabsf(k)) * 1.0001f + 1e-5f;
+    float rmin = (float)(a * (1.0 - e));
+    float ci2 = (float)(ci * ci), si2 = 1.0f - ci2;
+    float lo, hi;
+    float full = 1.5f * (float)P;
+    if (rmin * (float)fabs(ci) >= rr) {
+        lo = 1.0f;
+        hi = -1.0f;   // never in transit
+    } else {
+        float s2 = (rr * rr / (rmin * rmin) - ci2) / fmaxf(si2, 1e-30f);
+        if (s2 >= 1.0f) {
+            lo = -full;
+            hi = full;
+        } else {
+            float thw = asinf(sqrtf(fmaxf(s2, 0.0f))) * 1.001f + 1e-5f;
+            float margin = half_exp + 1e-6f + 1e-6f * (float)P;
+            if (!ecc) {
+                lo = -thw / r.nang - margin;
+                hi = thw / r.nang + margin;
+            } else {
+                float ef = (float)e, ftrf = (float)ftr;
+                float se2 = sqrtf(1.0f - ef), se1 = sqrtf(1.0f + ef);
+                float El = 2.0f * atan2f(se2 * sinf(0.5f * (ftrf - thw)), se1 * cosf(0.5f * (ftrf - thw)));
+                float Eh = 2.0f * atan2f(se2 * sinf(0.5f * (ftrf + thw)), se1 * cosf(0.5f * (ftrf + thw)));
+                float Mtr = (float)(Etr - e * sE);
+                float Ml = wrap_neg(El - ef * sinf(El) - Mtr);
+                float Mh = wrap_pos(Eh - ef * sinf(Eh) - Mtr);
+                if (Mh - Ml >= 3.0f) {
+                    lo = -full;
+                    hi = full;
+                } else {
+                    lo = Ml * 1.0005f / r.nang - margin;
+                    hi = Mh * 1.0005f / r.nang + margin;
+                }
+            }
+        }
+    }
+    r.win_lo = lo;
+    r.win_hi = hi;
+    *out = r;
+}
+
+
 // Warp-aggregated append to a shared-memory queue; returns the slot.
 __device__ __forceinline__ int warp_append(int *counter, bool pred)
 {
