@@ -82,6 +82,9 @@ def _lib():
                 ("pto_flux_theta", _D, [_D, _PD, _I, _D]),
                 ("pto_flux_grad", _D, [_D, _PD, _I, _D, _PD]),
                 ("pto_ssr_grad", None, [_PD, _I, _PD, _I, _I, _D, _PD, _PD, _PD, _PD, _I]),
+                ("pto_mlp_nparams", _I, []),
+                ("pto_mlp_forward", None, [_PD, _PD, _I, _PD]),
+                ("pto_mlp_loss_grad", _D, [_PD, _PD, _PD, _I, _PD]),
             ]:
                 fn = getattr(lib, name)
                 fn.restype = res
@@ -300,3 +303,27 @@ def ssr_grad(t, th, y, wt=None, n_ss=1, t_exp=0.0, n_threads=0):
     _lib().pto_ssr_grad(_ptr(t), t.size, _ptr(th), n_v, n_ss, t_exp, _ptr(y), _ptr(wt), _ptr(ssr), _ptr(grad),
                         n_threads)
     return ssr, grad
+
+
+# ---------------------------------------------------------------- surrogate network
+def mlp_nparams():
+    return _lib().pto_mlp_nparams()
+
+
+def mlp_forward(params, X):
+    """y [n, 2] of the 2-128-128-128-2 SiLU network (flattened FP64 params)."""
+    p = _arr(params, mlp_nparams())
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, 2))
+    Y = np.zeros_like(X)
+    _lib().pto_mlp_forward(_ptr(p), _ptr(X), X.shape[0], _ptr(Y))
+    return Y
+
+
+def mlp_loss_grad(params, X, T):
+    """(loss, grad) for L = mean_i sum_o (y_io - t_io)^2."""
+    p = _arr(params, mlp_nparams())
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, 2))
+    T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(-1, 2))
+    g = np.zeros(p.size)
+    loss = _lib().pto_mlp_loss_grad(_ptr(p), _ptr(X), _ptr(T), X.shape[0], _ptr(g))
+    return loss, g

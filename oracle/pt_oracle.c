@@ -717,3 +717,105 @@ void pto_ssr_grad(const double *t, int n_t, const double *th, int n_v, int n_ss,
         for (int j = 0; j < 9; ++j) grad[(size_t)v * 9 + j] = G[j];
     }
 }
+
+
+/* ------------------------------------------------------------------------
+ * Surrogate network (not in the paper; its analogue there is the
+ * interpolation tables of Sec. 2.2.3): a multilayer perceptron
+ * 2 -> 128 -> 128 -> 128 -> 2 with SiLU activations, silu(x) = x / (1 + e^-x).
+ * Parameters, flattened in this order (FP64 here):
+ *   W1[128][2], b1[128], W2[128][128], b2[128], W3[128][128], b3[128],
+ *   W4[2][128], b4[2]                                  (33,666 values)
+ * Loss: L = (1/n) sum_i sum_o (y_io - t_io)^2.
+ * ---------------------------------------------------------------------- */
+#define PTO_H 128
+#define PTO_NPAR (PTO_H * 2 + PTO_H + PTO_H * PTO_H + PTO_H + PTO_H * PTO_H + PTO_H + 2 * PTO_H + 2)
+
+int pto_mlp_nparams(void) { return PTO_NPAR; }
+
+static double silu(double x) { return x / (1.0 + exp(-x)); }
+
+static double dsilu(double x)
+{
+    double s = 1.0 / (1.0 + exp(-x));
+    return s * (1.0 + x * (1.0 - s));
+}
+
+/* forward for one input; z[3][H] and h[3][H] keep pre-activations and
+ * activations of the hidden layers (for the backward pass) */
+static void mlp_fwd(const double *p, const double *x, double *y, double z[3][PTO_H], double h[3][PTO_H])
+{
+    const double *W1 = p, *b1 = W1 + 2 * PTO_H, *W2 = b1 + PTO_H, *b2 = W2 + PTO_H * PTO_H;
+    const double *W3 = b2 + PTO_H, *b3 = W3 + PTO_H * PTO_H, *W4 = b3 + PTO_H, *b4 = W4 + 2 * PTO_H;
+    for (int j = 0; j < PTO_H; ++j) {
+        z[0][j] = W1[2 * j] * x[0] + W1[2 * j + 1] * x[1] + b1[j];
+        h[0][j] = silu(z[0][j]);
+    }
+    const double *Ws[2] = {W2, W3}, *bs[2] = {b2, b3};
+    for (int l = 1; l < 3; ++l) {
+        for (int j = 0; j < PTO_H; ++j) {
+            double a = bs[l - 1][j];
+            for (int i = 0; i < PTO_H; ++i) a += Ws[l - 1][j * PTO_H + i] * h[l - 1][i];
+            z[l][j] = a;
+            h[l][j] = silu(a);
+        }
+    }
+    for (int o = 0; o < 2; ++o) {
+        double a = b4[o];
+        for (int i = 0; i < PTO_H; ++i) a += W4[o * PTO_H + i] * h[2][i];
+        y[o] = a;
+    }
+}
+
+void pto_mlp_forward(const double *p, const double *X, int n, double *Y)
+{
+    double z[3][PTO_H], h[3][PTO_H];
+    for (int i = 0; i < n; ++i) mlp_fwd(p, X + 2 * i, Y + 2 * i, z, h);
+}
+
+/* loss and its gradient with respect to every parameter (backpropagation) */
+double pto_mlp_loss_grad(const double *p, const double *X, const double *T, int n, double *g)
+{
+    const double *W2 = p + 3 * PTO_H, *W3 = W2 + PTO_H * PTO_H + PTO_H, *W4 = W3 + PTO_H * PTO_H + PTO_H;
+    double *gW1 = g, *gb1 = gW1 + 2 * PTO_H, *gW2 = gb1 + PTO_H, *gb2 = gW2 + PTO_H * PTO_H;
+    double *gW3 = gb2 + PTO_H, *gb3 = gW3 + PTO_H * PTO_H, *gW4 = gb3 + PTO_H, *gb4 = gW4 + 2 * PTO_H;
+    for (int i = 0; i < PTO_NPAR; ++i) g[i] = 0.0;
+    double loss = 0.0;
+    double z[3][PTO_H], h[3][PTO_H], y[2], dz[PTO_H], dh[PTO_H];
+    for (int s = 0; s < n; ++s) {
+        const double *x = X + 2 * s;
+        mlp_fwd(p, x, y, z, h);
+        double dy[2];
+        for (int o = 0; o < 2; ++o) {
+            double r = y[o] - T[2 * s + o];
+            loss += r * r;
+            dy[o] = 2.0 * r / n;
+        }
+        for (int o = 0; o < 2; ++o) {
+            gb4[o] += dy[o];
+            for (int i = 0; i < PTO_H; ++i) gW4[o * PTO_H + i] += dy[o] * h[2][i];
+        }
+        for (int i = 0; i < PTO_H; ++i) dh[i] = W4[i] * dy[0] + W4[PTO_H + i] * dy[1];
+        const double *Ws[2] = {W2, W3};
+        double *gWs[2] = {gW2, gW3}, *gbs[2] = {gb2, gb3};
+        for (int l = 2; l >= 1; --l) {
+            for (int j = 0; j < PTO_H; ++j) dz[j] = dh[j] * dsilu(z[l][j]);
+            for (int j = 0; j < PTO_H; ++j) {
+                gbs[l - 1][j] += dz[j];
+                for (int i = 0; i < PTO_H; ++i) gWs[l - 1][j * PTO_H + i] += dz[j] * h[l - 1][i];
+            }
+            for (int i = 0; i < PTO_H; ++i) {
+                double a = 0.0;
+                for (int j = 0; j < PTO_H; ++j) a += Ws[l - 1][j * PTO_H + i] * dz[j];
+                dh[i] = a;
+            }
+        }
+        for (int j = 0; j < PTO_H; ++j) {
+            double d = dh[j] * dsilu(z[0][j]);
+            gb1[j] += d;
+            gW1[2 * j] += d * x[0];
+            gW1[2 * j + 1] += d * x[1];
+        }
+    }
+    return loss / n;
+}
