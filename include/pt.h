@@ -233,6 +233,80 @@ int pt_batch_plan_info(pt_batch_plan plan, int *tile, int *ctas_per_sm, int *n_i
 int pt_batch_plan_destroy(pt_batch_plan plan);
 
 /* ------------------------------------------------------------------------
+ * Surrogate network for the ingress/egress Mandel-Agol terms (not in the
+ * paper; its analogue there is the interpolation tables of Sec. 2.2.3).
+ * A multilayer perceptron 2 -> 128 -> 128 -> 128 -> 2 with SiLU
+ * activations, silu(x) = x / (1 + exp(-x)), maps normalised (k, s) to
+ * normalised (lambda_d / k^2, eta_d / k^2) over the ingress/egress band
+ * z = |1 - k| + 2 min(k, 1) s, s in [0, 1].  Parameters (FP32, device),
+ * flattened:  W1[128][2] b1[128] W2[128][128] b2[128] W3[128][128] b3[128]
+ * W4[2][128] b4[2].
+ *
+ * Training entry points (FP32 SIMT kernels):
+ *   pt_sur_datagen     n samples (k, s) from a counter-based generator
+ *                      (splitmix64 of seed and index offset..offset+n-1),
+ *                      targets from the exact FP32 kernel, written as
+ *                      X[n][2] = ((k - norm[0])/norm[1], 2s - 1),
+ *                      T[n][2] = ((ld/k^2 - norm[2])/norm[3], (ed/k^2 - norm[4])/norm[5]),
+ *                      kz[n][2] = (k, z) (kz may be NULL)
+ *   pt_mlp_forward     Y[n][2] for inputs X (FP32 reference forward; qat as below)
+ *   pt_mlp_loss_grad   loss = mean_i sum_o (y - t)^2 and its gradient; with
+ *                      qat != 0 the tensor-core layers' operands (h1, h2,
+ *                      W2, W3) are rounded to BF16 in the forward pass, as
+ *                      inference serves them (straight-through gradient)
+ *   pt_mlp_adam        one Adam step (bias-corrected, step >= 1)
+ * work: pt_mlp_work_bytes(n).  Reductions are deterministic.
+ * ---------------------------------------------------------------------- */
+#define PT_MLP_HIDDEN 128
+#define PT_MLP_NPARAMS 33666
+
+size_t pt_mlp_work_bytes(int n);
+int pt_sur_datagen(unsigned long long seed, size_t offset, size_t n, float k_lo, float k_hi, const float *norm_dev,
+                   float *X_dev, float *T_dev, float *kz_dev, pt_stream_t stream);
+int pt_mlp_forward(const float *params_dev, const float *X_dev, int n, int qat, float *Y_dev, void *work_dev,
+                   size_t work_bytes, pt_stream_t stream);
+int pt_mlp_loss_grad(const float *params_dev, const float *X_dev, const float *T_dev, int n, int qat,
+                     float *grad_dev, float *loss_dev, void *work_dev, size_t work_bytes, pt_stream_t stream);
+int pt_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int step, float lr,
+                float beta1, float beta2, float eps, pt_stream_t stream);
+
+/* Serving the surrogate (BF16 tensor cores, tcgen05.mma, FP32 accumulation):
+ *   pt_sur_model_create  copies FP32 parameters (device), packs W2 and W3 to
+ *                        BF16 in the tensor-core operand layout, and keeps
+ *                        the normalisation (norm[6] as in pt_sur_datagen), the
+ *                        k range of the band and an error-bound table
+ *                        (host, [nk][ns] over k in [k_lo, k_hi] x s in [0,1);
+ *                        1 = use the exact kernel in that cell).  Allocates
+ *                        device memory; pt_sur_model_destroy frees it.
+ *   pt_ma_surrogate      drop-in for pt_ma_terms: (lambda_e, lambda_d + 2/3
+ *                        Theta(k - z), eta_d) for n pairs (k, z).  Points in
+ *                        the band and in unmarked cells take lambda_d and
+ *                        eta_d from the network (lambda_e exact); all others
+ *                        take the exact FP32 kernel and are counted in
+ *                        *n_fallback_dev (optional device int).
+ *   pt_sur_mlp_eval      raw network outputs Y[n][2] for normalised inputs
+ *                        X[n][2] on the tensor-core path.
+ *   pt_sur_cell_errors   per-cell maximum over points of
+ *                        4 |ld_sur - ld_ref| + 2 |ed_sur - ed_ref| (a bound of
+ *                        the flux error for q1, q2 in [0, 1]), atomically
+ *                        maxed into cell_max[nk][ns] (caller zeroes it).
+ *   pt_sur_model_error   1 if a tensor-core wait ever timed out (the kernel
+ *                        then skipped its remaining tiles), else 0.
+ * ---------------------------------------------------------------------- */
+typedef struct pt_sur_model_s *pt_sur_model;
+
+int pt_sur_model_create(const float *params_dev, const float *norm, float k_lo, float k_hi,
+                        const unsigned char *table, int nk, int ns, pt_sur_model *model_out);
+int pt_sur_model_destroy(pt_sur_model model);
+int pt_ma_surrogate(pt_sur_model model, const float *k_dev, const float *z_dev, size_t n, float *lam_e_dev,
+                    float *lam_d_dev, float *eta_d_dev, int *n_fallback_dev, pt_stream_t stream);
+int pt_sur_mlp_eval(pt_sur_model model, const float *X_dev, size_t n, float *Y_dev, pt_stream_t stream);
+int pt_sur_cell_errors(const float *k_dev, const float *z_dev, const float *ld_ref_dev, const float *ed_ref_dev,
+                       const float *ld_sur_dev, const float *ed_sur_dev, size_t n, float k_lo, float k_hi, int nk,
+                       int ns, float *cell_max_dev, pt_stream_t stream);
+int pt_sur_model_error(pt_sur_model model, int *err_host);
+
+/* ------------------------------------------------------------------------
  * pt_ma_quad without a work buffer.  The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory -- e.g. a host
  * program whose device memory is all owned by its own fixed pool, or a tight

@@ -263,6 +263,22 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
     *ed = e_out;
 }
 
+// lambda_e alone (the lens area over pi), for callers that take lambda_d and
+// eta_d from elsewhere: the same geometry as ma_terms.
+__device__ __forceinline__ float lens_le(float p, float z)
+{
+    if (!(z < 1.0f + p) || !(p > 0.0f)) return 0.0f;
+    if (p >= 1.0f && z <= p - 1.0f) return 1.0f;
+    float d = (z - 1.0f) + p;
+    if (d <= 0.0f) return p * p;
+    float p2 = p * p, z2 = z * z;
+    float oma = (1.0f - z + p) * (1.0f + z - p);
+    float fa = sqrtf(fmaxf(0.0f, oma * d * (1.0f + z + p)));
+    float k1 = atan2f(fa, 1.0f - p2 + z2);
+    float k0 = atan2f(fa, p2 + z2 - 1.0f);
+    return (p2 * k0 + k1 - 0.5f * fa) * (1.0f / PT_PI_F);
+}
+
 // Quadratic-law weights of Eq. (ma_model): f = 1 - (we le + wd ld + wn ed),
 // with c = u1 + 2 u2 and the normalisation 1 - u1/3 - u2/6.
 __device__ __forceinline__ void ma_weights(float u1, float u2, float *we, float *wd, float *wn)
