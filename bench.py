@@ -215,6 +215,64 @@ def bench_batched(pt, torch, dev, stream, K, flush):
     return out
 
 
+def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000):
+    """Surrogate network: trained here on 1e7 exact-kernel samples (40 epochs,
+    the library's own kernels), error-bound table from 4e6 validation points,
+    then 1e9 band points through pt_ma_surrogate (BF16 tensor cores + exact
+    fallback) against the exact FP32 kernel pt_ma_terms on the same points."""
+    import paper_1504_07433_gb300.surrogate as S
+    t0 = time.perf_counter()
+    X, T, _ = S.datagen(10_000_000, seed=1504, device=dev)
+    tr = S.Trainer(S.init_params(0, device=dev), batch=16384, device=dev)
+    tr.fit(X, T, epochs=40, lr0=1e-3, lr1=1e-6, qat_epochs=3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, T
+    table, cm = S.build_table(tr.p, nk=64, ns=64, n_val=4_000_000, threshold=5e-6)
+    model = S.SurrogateModel(tr.p, table)
+    k, z = S.validation_points(n_infer, seed=5, device=dev)
+    outs = tuple(torch.empty_like(z) for _ in range(3))
+    work = torch.empty(int(S.lib().pt_sur_work_bytes(z.numel())), dtype=torch.uint8, device=dev)
+    nfb = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def run_exact():
+        from paper_1504_07433_gb300 import _check, _ptr, _stream
+        _check(S.lib().pt_ma_terms(_ptr(k), _ptr(z), z.numel(), _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2]),
+                                   _stream()), "pt_ma_terms")
+
+    def run_sur():
+        model.terms(k, z, nfb, work, outs)
+
+    res = {}
+    for name, fn in (("exact", run_exact), ("surrogate", run_sur)):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(3):
+            nfb.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name] = float(np.mean(ms))
+    share = 1.0 - int(nfb.item()) / n_infer
+    out = {"workload": "1e9 (k, z) points over k in [0.01, 0.3], z in [|1-k|, 1+k]",
+           "train_s": t_train, "train_samples": 10_000_000, "epochs": 40,
+           "table_cells_exact": float(table.mean()), "network_share": share,
+           "exact_ms": res["exact"], "surrogate_ms": res["surrogate"],
+           "exact_points_per_s": n_infer / (res["exact"] * 1e-3),
+           "surrogate_points_per_s": n_infer / (res["surrogate"] * 1e-3),
+           "gain_vs_exact": res["exact"] / res["surrogate"], "timed_out": model.timed_out(),
+           "tensor_tflops": share * n_infer * 2 * 2 * 128 * 128 / (res["surrogate"] * 1e-3) / 1e12}
+    model.close()
+    del k, z, outs, work
+    torch.cuda.empty_cache()
+    return out
+
+
 def reference_main(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -404,10 +462,11 @@ def main():
                 "peak_source": "FP32 lanes 152 SM x 128 x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_max, peak_src),
                 "algorithmic_flops_per_launch": flops, "in_transit_evaluations": n_intr}
 
-    adjoint = batched = None
+    adjoint = batched = surrogate = None
     if not args.no_extra:
         adjoint = bench_adjoint(pt, torch, dev, stream, K, flush)
         batched = bench_batched(pt, torch, dev, stream, K, flush)
+        surrogate = bench_surrogate(torch, dev, stream)
 
     cpu = None
     max_err = None
@@ -434,7 +493,7 @@ def main():
                 "components_ms": {"ma_quad": float(np.mean(ma_ms)), "gimenez": g_mean_ms},
                 "max_abs_err_vs_oracle": max_err,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint,
-                "batched": batched,
+                "batched": batched, "surrogate": surrogate,
                 "gpu_launches": 5 * K, "clocks": dict(clocks, window="%.1f s of untimed steps + the timed region"
                                                       % args.heat_s) if clocks else None,
                 "wall_s_timed": wall}

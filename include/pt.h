@@ -246,9 +246,9 @@ int pt_batch_plan_destroy(pt_batch_plan plan);
  *   pt_sur_datagen     n samples (k, s) from a counter-based generator
  *                      (splitmix64 of seed and index offset..offset+n-1),
  *                      targets from the exact FP32 kernel, written as
- *                      X[n][2] = ((k - norm[0])/norm[1], 2s - 1),
+ *                      X[n][2] = ((k - norm[0])/norm[1], (2/pi) acos(1 - 2s) - 1),
  *                      T[n][2] = ((ld/k^2 - norm[2])/norm[3], (ed/k^2 - norm[4])/norm[5]),
- *                      kz[n][2] = (k, z) (kz may be NULL)
+ *                      kz[n][2] = (k, z); X, T or kz may be NULL (not all)
  *   pt_mlp_forward     Y[n][2] for inputs X (FP32 reference forward; qat as below)
  *   pt_mlp_loss_grad   loss = mean_i sum_o (y - t)^2 and its gradient; with
  *                      qat != 0 the tensor-core layers' operands (h1, h2,
@@ -282,8 +282,11 @@ int pt_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v
  *                        Theta(k - z), eta_d) for n pairs (k, z).  Points in
  *                        the band and in unmarked cells take lambda_d and
  *                        eta_d from the network (lambda_e exact); all others
- *                        take the exact FP32 kernel and are counted in
- *                        *n_fallback_dev (optional device int).
+ *                        take the exact FP32 kernel (computed while the points
+ *                        are classified) and are counted in *n_fallback_dev
+ *                        (optional device int, caller zeroes it); the
+ *                        network's points are compacted into a list in
+ *                        work_dev (pt_sur_work_bytes(n) bytes).
  *   pt_sur_mlp_eval      raw network outputs Y[n][2] for normalised inputs
  *                        X[n][2] on the tensor-core path.
  *   pt_sur_cell_errors   per-cell maximum over points of
@@ -298,8 +301,10 @@ typedef struct pt_sur_model_s *pt_sur_model;
 int pt_sur_model_create(const float *params_dev, const float *norm, float k_lo, float k_hi,
                         const unsigned char *table, int nk, int ns, pt_sur_model *model_out);
 int pt_sur_model_destroy(pt_sur_model model);
+size_t pt_sur_work_bytes(size_t n);
 int pt_ma_surrogate(pt_sur_model model, const float *k_dev, const float *z_dev, size_t n, float *lam_e_dev,
-                    float *lam_d_dev, float *eta_d_dev, int *n_fallback_dev, pt_stream_t stream);
+                    float *lam_d_dev, float *eta_d_dev, int *n_fallback_dev, void *work_dev, size_t work_bytes,
+                    pt_stream_t stream);
 int pt_sur_mlp_eval(pt_sur_model model, const float *X_dev, size_t n, float *Y_dev, pt_stream_t stream);
 int pt_sur_cell_errors(const float *k_dev, const float *z_dev, const float *ld_ref_dev, const float *ed_ref_dev,
                        const float *ld_sur_dev, const float *ed_sur_dev, size_t n, float k_lo, float k_hi, int nk,

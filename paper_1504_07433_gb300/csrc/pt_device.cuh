@@ -263,6 +263,14 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
     *ed = e_out;
 }
 
+// Network coordinate across the ingress/egress band: theta = acos(1 - 2 s)
+// mapped to [-1, 1].  Near both contacts (s -> 0, s -> 1) the MA terms
+// behave like powers of sqrt(s) and sqrt(1 - s); in theta they are regular.
+__device__ __forceinline__ float band_coord(float s)
+{
+    return acosf(fminf(1.0f, fmaxf(-1.0f, 1.0f - 2.0f * s))) * (2.0f / PT_PI_F) - 1.0f;
+}
+
 // lambda_e alone (the lens area over pi), for callers that take lambda_d and
 // eta_d from elsewhere: the same geometry as ma_terms.
 __device__ __forceinline__ float lens_le(float p, float z)

@@ -78,10 +78,14 @@ __global__ void datagen_kernel(uint64_t seed, size_t offset, size_t n, float k_l
     float le, ld, ed;
     pt::ma_terms(k, z, &le, &ld, &ed);
     float ik2 = 1.0f / (k * k);
-    X[2 * i] = (k - norm[0]) / norm[1];
-    X[2 * i + 1] = 2.0f * s - 1.0f;
-    T[2 * i] = (ld * ik2 - norm[2]) / norm[3];
-    T[2 * i + 1] = (ed * ik2 - norm[4]) / norm[5];
+    if (X) {
+        X[2 * i] = (k - norm[0]) / norm[1];
+        X[2 * i + 1] = pt::band_coord(s);
+    }
+    if (T) {
+        T[2 * i] = (ld * ik2 - norm[2]) / norm[3];
+        T[2 * i + 1] = (ed * ik2 - norm[4]) / norm[5];
+    }
     if (kz) {
         kz[2 * i] = k;
         kz[2 * i + 1] = z;
@@ -461,7 +465,7 @@ int pt_sur_datagen(unsigned long long seed, size_t offset, size_t n, float k_lo,
                    float *X, float *T, float *kz, pt_stream_t stream)
 {
     if (n == 0) return PT_OK;
-    if (!norm || !X || !T || !(k_lo > 0.0f) || !(k_hi >= k_lo) || k_hi > 1.0f) return PT_ERR_ARG;
+    if (!norm || (!X && !T && !kz) || !(k_lo > 0.0f) || !(k_hi >= k_lo) || k_hi > 1.0f) return PT_ERR_ARG;
     size_t blocks = (n + 255) / 256;
     if (blocks > 0x7fffffffULL) return PT_ERR_ARG;
     datagen_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(seed, offset, n, k_lo, k_hi, norm, X, T, kz);

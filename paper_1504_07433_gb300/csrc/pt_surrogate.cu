@@ -38,7 +38,7 @@ namespace {
 
 constexpr int H = PT_MLP_HIDDEN;
 constexpr int TILE = 128;                 // points per tile = MMA M
-constexpr int NTHR = 128;                 // 4 warps
+constexpr int NTHR = 256;                 // 8 warps
 constexpr int TILE_BYTES = H * H * 2;     // one 128 x 128 BF16 operand (32 KB)
 constexpr int TMEM_COLS = 128;            // FP32 accumulator 128 x 128
 constexpr long long WAIT_LIMIT = 1 << 22; // bounded mbarrier polls
@@ -181,16 +181,54 @@ struct SurModel {
 
 struct SurArgs {
     SurModel m;
-    int mode;                  // 0: network outputs Y from X; 1: surrogate MA terms from (k, z)
+    int mode;                  // 0: network outputs Y from X; 1: surrogate MA terms for listed points
     const float *X;            // mode 0: [n][2]
     float *Y;                  // mode 0: [n][2]
     const float *k, *z;        // mode 1
     float *le, *ld, *ed;       // mode 1
-    size_t n;
-    int *n_fallback;
+    const int *list;           // mode 1: indices of the points the network serves
+    const int *count;          // mode 1: number of listed points (device)
+    size_t n;                  // mode 0: number of points
     int *err;                  // set to 1 on an mbarrier time-out
 };
 
+// Classify every point: outside the band or in a marked cell -> exact
+// kernel here and now; otherwise append to the network's list.
+__global__ void classify_kernel(SurModel m, const float *k, const float *z, size_t n, float *le, float *ld,
+                                float *ed, int *list, int *count, int *n_fallback)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool net = false;
+    if (i < n) {
+        float kk = k[i], zz = fabsf(z[i]);
+        float s = (zz - fabsf(1.0f - kk)) / (2.0f * fminf(kk, 1.0f));
+        net = kk >= m.k_lo && kk <= m.k_hi && s >= 0.0f && s < 1.0f;
+        if (net) {
+            int ck = min(m.nk - 1, (int)((kk - m.k_lo) / (m.k_hi - m.k_lo) * m.nk));
+            int cs = min(m.ns - 1, (int)(s * m.ns));
+            net = m.table[ck * m.ns + cs] == 0;
+        }
+        if (!net) {
+            float a, b, c;
+            pt::ma_terms(kk, zz, &a, &b, &c);
+            le[i] = a;
+            ld[i] = b;
+            ed[i] = c;
+        }
+    }
+    // warp-aggregated appends
+    unsigned mask = __ballot_sync(0xffffffffu, net);
+    int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && mask) base = atomicAdd(count, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (net) list[base + __popc(mask & ((1u << lane) - 1u))] = (int)i;
+    unsigned fb = __ballot_sync(0xffffffffu, i < n && !net);
+    if (lane == 0 && fb && n_fallback) atomicAdd(n_fallback, __popc(fb));
+}
+
+// Thread layout: 8 warps; warp w serves tile rows 32 (w % 4) .. +31 (the
+// tensor-memory lanes it may read) and columns 64 (w / 4) .. +63.
 __global__ void __launch_bounds__(NTHR) sur_kernel(SurArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -202,12 +240,14 @@ __global__ void __launch_bounds__(NTHR) sur_kernel(SurArgs A)
     float *sB2 = sB1 + H;
     float *sB3 = sB2 + H;
     float *sW4 = sB3 + H;                                           // [2][128]
+    float *sY = sW4 + 2 * H;                                        // [128][2] partial outputs
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_base;
-    __shared__ int s_abort, s_fb;
+    __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    // stage weights (once per CTA)
+    const int row = 32 * (warp & 3) + (tid & 31);
+    const int half = warp >> 2, c0 = 64 * half;
     {
         const uint4 *g2 = reinterpret_cast<const uint4 *>(A.m.w2);
         const uint4 *g3 = reinterpret_cast<const uint4 *>(A.m.w3);
@@ -230,7 +270,6 @@ __global__ void __launch_bounds__(NTHR) sur_kernel(SurArgs A)
     if (tid == 0) {
         mbar_init(&bar, 1);
         s_abort = 0;
-        s_fb = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -245,40 +284,33 @@ __global__ void __launch_bounds__(NTHR) sur_kernel(SurArgs A)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t aA = smem_u32(sA), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);   // this warp's lanes
+    const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
     const float b4_0 = A.m.p32[OFF_B4], b4_1 = A.m.p32[OFF_B4 + 1];
-    const size_t n_tiles = (A.n + TILE - 1) / TILE;
-    uint32_t phase = 0;     // parity of the next mbarrier phase to complete
-    int my_fb = 0;
+    const size_t n = (A.mode == 0) ? A.n : (size_t)(*A.count);
+    const size_t n_tiles = (n + TILE - 1) / TILE;
+    uint32_t phase = 0;   // parity of the next mbarrier phase to complete
 
     for (size_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const size_t i = tile * TILE + tid;
-        const bool valid = i < A.n;
-        // ---- inputs
-        float x0 = 0.0f, x1 = 0.0f, kk = 0.1f, zz = 2.0f;
-        bool in_band = false;
-        if (A.mode == 0) {
-            if (valid) {
+        const size_t slot = tile * TILE + row;
+        const bool valid = slot < n;
+        size_t i = slot;
+        float x0 = 0.0f, x1 = 0.0f, kk = 0.1f, zz = 1.0f;
+        if (valid) {
+            if (A.mode == 0) {
                 x0 = A.X[2 * i];
                 x1 = A.X[2 * i + 1];
-            }
-        } else if (valid) {
-            kk = A.k[i];
-            zz = fabsf(A.z[i]);
-            float lo = fabsf(1.0f - kk), w = 2.0f * fminf(kk, 1.0f);
-            float s = (zz - lo) / w;
-            in_band = kk >= A.m.k_lo && kk <= A.m.k_hi && s >= 0.0f && s < 1.0f;
-            x0 = (kk - A.m.norm[0]) / A.m.norm[1];
-            x1 = 2.0f * s - 1.0f;
-            if (in_band) {
-                int ck = min(A.m.nk - 1, (int)((kk - A.m.k_lo) / (A.m.k_hi - A.m.k_lo) * A.m.nk));
-                int cs = min(A.m.ns - 1, (int)(s * A.m.ns));
-                if (A.m.table[ck * A.m.ns + cs]) in_band = false;
+            } else {
+                i = (size_t)A.list[slot];
+                kk = A.k[i];
+                zz = fabsf(A.z[i]);
+                float s = (zz - fabsf(1.0f - kk)) / (2.0f * fminf(kk, 1.0f));
+                x0 = (kk - A.m.norm[0]) / A.m.norm[1];
+                x1 = pt::band_coord(fminf(1.0f, fmaxf(0.0f, s)));
             }
         }
-        // ---- layer 1 -> BF16 operand rows (row = tid)
-#pragma unroll 4
-        for (int k0 = 0; k0 < H; k0 += 8) {
+        // ---- layer 1 (this thread's 64 columns) -> BF16 operand
+#pragma unroll 2
+        for (int k0 = c0; k0 < c0 + 64; k0 += 8) {
             __align__(16) __nv_bfloat16 h8[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -286,13 +318,12 @@ __global__ void __launch_bounds__(NTHR) sur_kernel(SurArgs A)
                 float zj = fmaf(sW1[2 * j], x0, fmaf(sW1[2 * j + 1], x1, sB1[j]));
                 h8[q] = __float2bfloat16_rn(silu_fast(zj));
             }
-            *reinterpret_cast<uint4 *>(sA + op_offset(tid, k0)) = *reinterpret_cast<uint4 *>(h8);
+            *reinterpret_cast<uint4 *>(sA + op_offset(row, k0)) = *reinterpret_cast<uint4 *>(h8);
         }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        // ---- layer 2 on the tensor cores
         if (tid == 0 && !s_abort) issue_layer(tmem, aA, aW2, &bar);
         bool ok = mbar_wait(&bar, phase);
         phase ^= 1u;
@@ -300,24 +331,24 @@ __global__ void __launch_bounds__(NTHR) sur_kernel(SurArgs A)
         tc_fence_after();
         __syncthreads();
         if (s_abort) break;
-        // ---- epilogue 2: bias + SiLU -> BF16 operand (overwrites layer-1 activations)
+        // ---- epilogue 2
 #pragma unroll 1
-        for (int c = 0; c < H; c += 32) {
+        for (int c = 0; c < 64; c += 32) {
             float v[32];
             tmem_ld32(trow + (uint32_t)c, v);
 #pragma unroll
             for (int k0 = 0; k0 < 32; k0 += 8) {
                 __align__(16) __nv_bfloat16 h8[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) h8[q] = __float2bfloat16_rn(silu_fast(v[k0 + q] + sB2[c + k0 + q]));
-                *reinterpret_cast<uint4 *>(sA + op_offset(tid, c + k0)) = *reinterpret_cast<uint4 *>(h8);
+                for (int q = 0; q < 8; ++q)
+                    h8[q] = __float2bfloat16_rn(silu_fast(v[k0 + q] + sB2[c0 + c + k0 + q]));
+                *reinterpret_cast<uint4 *>(sA + op_offset(row, c0 + c + k0)) = *reinterpret_cast<uint4 *>(h8);
             }
         }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        // ---- layer 3 on the tensor cores
         if (tid == 0 && !s_abort) issue_layer(tmem, aA, aW3, &bar);
         ok = mbar_wait(&bar, phase);
         phase ^= 1u;
@@ -325,57 +356,46 @@ __global__ void __launch_bounds__(NTHR) sur_kernel(SurArgs A)
         tc_fence_after();
         __syncthreads();
         if (s_abort) break;
-        // ---- epilogue 3 + layer 4 (FP32)
-        float y0 = b4_0, y1 = b4_1;
+        // ---- epilogue 3 + layer 4 partial sums over this thread's columns
+        float y0 = 0.0f, y1 = 0.0f;
 #pragma unroll 1
-        for (int c = 0; c < H; c += 32) {
+        for (int c = 0; c < 64; c += 32) {
             float v[32];
             tmem_ld32(trow + (uint32_t)c, v);
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-                float h = silu_acc(v[q] + sB3[c + q]);
-                y0 = fmaf(sW4[c + q], h, y0);
-                y1 = fmaf(sW4[H + c + q], h, y1);
+                int j = c0 + c + q;
+                float h = silu_acc(v[q] + sB3[j]);
+                y0 = fmaf(sW4[j], h, y0);
+                y1 = fmaf(sW4[H + j], h, y1);
             }
         }
+        if (half == 1) {
+            sY[2 * row] = y0;
+            sY[2 * row + 1] = y1;
+        }
         tc_fence_before();
-        __syncthreads();   // every warp has read the accumulator before the next tile's MMA
+        __syncthreads();   // partial sums exchanged; accumulator fully read before the next MMA
         tc_fence_after();
-        // ---- outputs
-        if (valid) {
+        if (half == 0 && valid) {
+            y0 += sY[2 * row] + b4_0;
+            y1 += sY[2 * row + 1] + b4_1;
             if (A.mode == 0) {
                 A.Y[2 * i] = y0;
                 A.Y[2 * i + 1] = y1;
             } else {
-                float le, ld, ed;
-                if (in_band) {          // network terms; lambda_e exact (elementary)
-                    float k2 = kk * kk;
-                    le = pt::lens_le(kk, zz);
-                    ld = k2 * fmaf(y0, A.m.norm[3], A.m.norm[2]);
-                    ed = k2 * fmaf(y1, A.m.norm[5], A.m.norm[4]);
-                } else {                // outside the band or in a marked cell: exact kernel
-                    pt::ma_terms(kk, zz, &le, &ld, &ed);
-                    ++my_fb;
-                }
-                A.le[i] = le;
-                A.ld[i] = ld;
-                A.ed[i] = ed;
+                float k2 = kk * kk;
+                A.le[i] = pt::lens_le(kk, zz);
+                A.ld[i] = k2 * fmaf(y0, A.m.norm[3], A.m.norm[2]);
+                A.ed[i] = k2 * fmaf(y1, A.m.norm[5], A.m.norm[4]);
             }
         }
     }
-    if (s_abort) {
-        // an MMA batch may still be in flight: wait for it (bounded) before
-        // the tensor memory is released
-        mbar_wait(&bar, phase ^ 1u);
-    }
-    if (my_fb) atomicAdd(&s_fb, my_fb);
+    if (s_abort) mbar_wait(&bar, phase ^ 1u);   // in-flight MMAs finish before the memory is freed
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) {
-        if (s_abort && A.err) atomicExch(A.err, 1);
-        if (s_fb && A.n_fallback) atomicAdd(A.n_fallback, s_fb);
-    }
+    if (tid == 0 && s_abort && A.err) atomicExch(A.err, 1);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TMEM_COLS)
                      : "memory");
@@ -411,7 +431,7 @@ __global__ void pack_weights_kernel(const float *W, __nv_bfloat16 *out)
     out[op_offset(r, k) / 2] = __float2bfloat16_rn(W[idx]);
 }
 
-size_t sur_smem() { return (size_t)3 * TILE_BYTES + (size_t)(2 * H + 3 * H + 2 * H) * sizeof(float); }
+size_t sur_smem() { return (size_t)3 * TILE_BYTES + (size_t)(2 * H + 3 * H + 2 * H + 2 * TILE) * sizeof(float); }
 
 }  // namespace
 
@@ -492,13 +512,13 @@ int pt_sur_model_destroy(pt_sur_model p)
     return PT_OK;
 }
 
-static int launch_sur(pt_sur_model p, SurArgs &a, size_t n, pt_stream_t stream)
+static int launch_sur(pt_sur_model p, SurArgs &a, size_t max_points, pt_stream_t stream)
 {
     a.m = p->m;
-    a.n = n;
     a.err = p->d_err;
-    size_t tiles = (n + TILE - 1) / TILE;
+    size_t tiles = (max_points + TILE - 1) / TILE;
     int grid = (int)(tiles < (size_t)p->grid ? tiles : (size_t)p->grid);
+    if (grid < 1) grid = 1;
     sur_kernel<<<grid, NTHR, sur_smem(), (cudaStream_t)stream>>>(a);
     return cuda_status("sur_kernel");
 }
@@ -512,15 +532,29 @@ int pt_sur_mlp_eval(pt_sur_model p, const float *X, size_t n, float *Y, pt_strea
     a.mode = 0;
     a.X = X;
     a.Y = Y;
+    a.n = n;
     return launch_sur(p, a, n, stream);
 }
 
+size_t pt_sur_work_bytes(size_t n) { return 256 + ((n * sizeof(int) + 255) & ~(size_t)255); }
+
 int pt_ma_surrogate(pt_sur_model p, const float *k, const float *z, size_t n, float *le, float *ld, float *ed,
-                    int *n_fallback, pt_stream_t stream)
+                    int *n_fallback, void *work, size_t work_bytes, pt_stream_t stream)
 {
     if (!p) return PT_ERR_ARG;
     if (n == 0) return PT_OK;
     if (!k || !z || !le || !ld || !ed) return PT_ERR_ARG;
+    if (n > 0x7fffffffULL) return PT_ERR_ARG;
+    if (!work || work_bytes < pt_sur_work_bytes(n)) return PT_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *count = (int *)work;
+    int *list = (int *)((char *)work + 256);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return pt_internal::set_error(PT_ERR_CUDA, "pt_ma_surrogate", cudaGetErrorString(e));
+    size_t blocks = (n + 255) / 256;
+    classify_kernel<<<(unsigned)blocks, 256, 0, s>>>(p->m, k, z, n, le, ld, ed, list, count, n_fallback);
+    int st = cuda_status("classify_kernel");
+    if (st) return st;
     SurArgs a{};
     a.mode = 1;
     a.k = k;
@@ -528,7 +562,8 @@ int pt_ma_surrogate(pt_sur_model p, const float *k, const float *z, size_t n, fl
     a.le = le;
     a.ld = ld;
     a.ed = ed;
-    a.n_fallback = n_fallback;
+    a.list = list;
+    a.count = count;
     return launch_sur(p, a, n, stream);
 }
 

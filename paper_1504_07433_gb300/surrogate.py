@@ -42,7 +42,8 @@ def _sig(lib):
         ("pt_sur_model_create", _c_int, [P, ctypes.POINTER(F), F, F, ctypes.POINTER(ctypes.c_ubyte), _c_int, _c_int,
                                          ctypes.POINTER(_c_void_p)]),
         ("pt_sur_model_destroy", _c_int, [P]),
-        ("pt_ma_surrogate", _c_int, [P, P, P, S, P, P, P, P, P]),
+        ("pt_ma_surrogate", _c_int, [P, P, P, S, P, P, P, P, P, S, P]),
+        ("pt_sur_work_bytes", S, [S]),
         ("pt_sur_mlp_eval", _c_int, [P, P, S, P, P]),
         ("pt_sur_cell_errors", _c_int, [P, P, P, P, P, P, S, F, F, _c_int, _c_int, P, P]),
         ("pt_sur_model_error", _c_int, [P, ctypes.POINTER(_c_int)]),
@@ -163,14 +164,17 @@ class SurrogateModel:
         self.handle = h
         self.nk, self.ns = nk, ns
 
-    def terms(self, k, z, n_fallback=None):
+    def terms(self, k, z, n_fallback=None, work=None, out=None):
         """(lambda_e, lambda_d', eta_d) like pt_ma_terms (pt_ma_surrogate)."""
         torch = _torch()
-        le = torch.empty_like(z)
-        ld = torch.empty_like(z)
-        ed = torch.empty_like(z)
+        if out is None:
+            out = (torch.empty_like(z), torch.empty_like(z), torch.empty_like(z))
+        le, ld, ed = out
+        need = int(lib().pt_sur_work_bytes(z.numel()))
+        if work is None or work.numel() < need:
+            work = torch.empty(need, dtype=torch.uint8, device=z.device)
         _check(lib().pt_ma_surrogate(self.handle, _ptr(k), _ptr(z), z.numel(), _ptr(le), _ptr(ld), _ptr(ed),
-                                     _ptr(n_fallback), _stream()), "pt_ma_surrogate")
+                                     _ptr(n_fallback), _ptr(work), work.numel(), _stream()), "pt_ma_surrogate")
         return le, ld, ed
 
     def network(self, X):

@@ -82,8 +82,8 @@ def test_datagen_targets_are_exact_terms(env):
     X, T = X.cpu().numpy(), T.cpu().numpy()
     k, z = kz[:, 0], kz[:, 1]
     assert np.all((k >= S.K_LO) & (k <= S.K_HI))
-    s = (X[:, 1] + 1) / 2
-    assert np.allclose(z, np.abs(1 - k) + 2 * k * s, atol=1e-6)
+    s = (1 - np.cos((X[:, 1] + 1) * np.pi / 2)) / 2       # inverse of the band coordinate
+    assert np.allclose(z, np.abs(1 - k) + 2 * k * s, atol=2e-6)
     ref = np.array([oracle.ma_terms(kk, zz) for kk, zz in zip(k, z)])
     ld = ref[:, 1] + np.where(k > z, 2 / 3, 0.0)
     ed = ref[:, 2]
