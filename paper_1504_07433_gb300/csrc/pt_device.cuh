@@ -198,11 +198,15 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
     float eta2 = 0.5f * p2 * (p2 + 2.0f * z2);
     bool inside = d < 0.0f;
 
-    float fa = sqrtf(fmaxf(0.0f, oma * bm1));       // 4 x triangle area
-    float k1 = atan2f(fa, 1.0f - p2 + z2);
-    float k0 = atan2f(fa, p2 + z2 - 1.0f);
-    float le_part = (p2 * k0 + k1 - 0.5f * fa) * (1.0f / pi);
-    float eta1 = (k1 + 2.0f * eta2 * k0 - 0.25f * (1.0f + 5.0f * p2 + z2) * fa) * (0.5f / pi);
+    // lens geometry: only the partial (and contact) cases need it
+    float le_part = p2, eta1 = eta2;
+    if (!inside) {
+        float fa = sqrtf(fmaxf(0.0f, oma * bm1));       // 4 x triangle area
+        float k1 = atan2f(fa, 1.0f - p2 + z2);
+        float k0 = atan2f(fa, p2 + z2 - 1.0f);
+        le_part = (p2 * k0 + k1 - 0.5f * fa) * (1.0f / pi);
+        eta1 = (k1 + 2.0f * eta2 * k0 - 0.25f * (1.0f + 5.0f * p2 + z2) * fa) * (0.5f / pi);
+    }
 
     // parameters of the shared elliptic evaluation
     float kc, cKp, cE, rho = 1.0f, cR = 0.0f, pref, cst = 0.0f;
@@ -340,20 +344,28 @@ __device__ __forceinline__ void make_geom_rec(double t0, double P, float a_f, fl
         w = w_f;
     }
     r.ecc = ecc ? 1.0f : 0.0f;
-    // conjunction anchor (FP64): f_tr = pi/2 - w, E_tr from tan(E/2) = sqrt((1-e)/(1+e)) tan(f/2)
+    // conjunction anchor: f_tr = pi/2 - w, E_tr from tan(E/2) = sqrt((1-e)/(1+e)) tan(f/2).
+    // FP32 suffices: the anchor's sine and cosine only scale the small
+    // differential terms of orbit_z (relative error ~1e-7 there), and the
+    // sky position at conjunction is zero by construction, not computed.
+    float ef = (float)e, wf = (float)w;
+    float ftrf = 0.5f * PT_PI_F - wf;
+    float Etrf = 2.0f * atan2f(sqrtf(1.0f - ef) * sinf(0.5f * ftrf), sqrtf(1.0f + ef) * cosf(0.5f * ftrf));
+    float sEf, cEf, swf, cwf;
+    sincosf(Etrf, &sEf, &cEf);
+    sincosf(wf, &swf, &cwf);
+    float sef = sqrtf((1.0f - ef) * (1.0f + ef)), af = (float)a;
     double ftr = 0.5 * PT_PI_D - w;
-    double Etr = 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * ftr), sqrt(1.0 + e) * cos(0.5 * ftr));
-    double sE = sin(Etr), cE = cos(Etr);
-    double sw = sin(w), cw = cos(w), se = sqrt(1.0 - e * e);
-    r.ecE = (float)(e * cE);
-    r.esE = (float)(e * sE);
-    r.cE = (float)cE;
-    r.sE = (float)sE;
-    r.Uc = (float)(a * cw);
-    r.Us = (float)(a * se * sw);
-    r.Vs = (float)(a * sw);
-    r.Vc = (float)(a * se * cw);
-    r.Vtr = (float)(a * (1.0 - e * cE));
+    double Etr = Etrf, sE = sEf;
+    r.ecE = ef * cEf;
+    r.esE = ef * sEf;
+    r.cE = cEf;
+    r.sE = sEf;
+    r.Uc = af * cwf;
+    r.Us = af * sef * swf;
+    r.Vs = af * swf;
+    r.Vc = af * sef * cwf;
+    r.Vtr = af * (1.0f - ef * cEf);
     r.pad0 = r.pad1 = r.pad2 = 0.0f;
     // Conservative window.  z^2 >= r_min^2 (sin^2(th) sin^2 i + cos^2 i) with
     // th = w + f - pi/2 and r_min = a (1 - e), so z > 1 + k whenever
@@ -375,6 +387,21 @@ __device__ __forceinline__ void make_geom_rec(double t0, double P, float a_f, fl
             hi = full;
         } else {
             float thw = asinf(sqrtf(fmaxf(s2, 0.0f))) * 1.001f + 1e-5f;
+            if (ecc && e > 0.0) {
+                // r = a (1 - e^2) / (1 + e cos f) is smallest where cos f is
+                // largest; over f in [f_tr - thw, f_tr + thw] that bound is
+                // much tighter than a (1 - e), and the window it gives
+                // (narrower, so the bound still holds on it) is conservative.
+                float ftr_f = (float)ftr;
+                float f1 = ftr_f - thw, f2 = ftr_f + thw;
+                float cmax = fmaxf(cosf(f1), cosf(f2));
+                float f0 = 6.28318530717958f * ceilf(f1 / 6.28318530717958f);   // first multiple of 2 pi >= f1
+                if (f0 <= f2) cmax = 1.0f;
+                float ef2 = (float)e;
+                float rmin2 = (float)a * (1.0f - ef2 * ef2) / (1.0f + ef2 * cmax) * 0.9999f;
+                float s2b = (rr * rr / (rmin2 * rmin2) - ci2) / fmaxf(si2, 1e-30f);
+                if (rmin2 > rmin && s2b < s2) thw = asinf(sqrtf(fmaxf(s2b, 0.0f))) * 1.001f + 1e-5f;
+            }
             float margin = half_exp + 1e-6f + 1e-6f * (float)P;
             if (!ecc) {
                 lo = -thw / r.nang - margin;

@@ -126,8 +126,7 @@ struct LcArgs {
     int n_tiles;
     int *n_bad;
     // Gimenez
-    const float4 *gcoef; // [N+1][n_j] (r1, r2, r3, 0)
-    const float *gT;     // [n_geom][N+1][n_j]
+    const float4 *gtab;  // [n_geom][N+1][n_j]: (r1_j, r2_j, r3_{j+1}, T_j)
     int N, n_j;
 };
 
@@ -295,31 +294,37 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 // carries all supersamples of its pair in registers, SB at a time.
 // ---------------------------------------------------------------------------
 template <int SB>
-__device__ __forceinline__ void gim_unit(const float4 *coef, const float *Tn, int n_j, int n, float b2,
-                                         const float *sx, const float *sq, int nss, float *acc_out)
+__device__ __forceinline__ void gim_unit(const float4 *tab, int n_j, int n, float b2, const float *sx,
+                                         const float *sq, int nss, float *acc_out)
 {
+    // Clenshaw's backward summation of S = sum_j T_j G_j with
+    // G_{j+1} = (r1_j + r2_j x) G_j + r3_j G_{j-1}, G_0 = 1, G_{-1} = 0:
+    //   b_j = T_j + (r1_j + r2_j x) b_{j+1} + r3_{j+1} b_{j+2},  S = b_0,
+    // three FMAs per term; tab[j] = (r1_j, r2_j, r3_{j+1}, T_j).
     float acc = 0.0f;
 #pragma unroll 1
     for (int s0 = 0; s0 < nss; s0 += SB) {
-        float x[SB], g[SB], gp[SB], sum[SB];
+        float x[SB], b1[SB], b2v[SB];
+        bool any = false;
 #pragma unroll
         for (int u = 0; u < SB; ++u) {
             int s = s0 + u;
             x[u] = (s < nss) ? sx[s] : 0.0f;
-            g[u] = 1.0f;
-            gp[u] = 0.0f;
-            sum[u] = Tn[0];
+            any |= (s < nss) && (sq[s] > 0.0f);
+            b1[u] = 0.0f;
+            b2v[u] = 0.0f;
         }
+        if (!any) continue;   // every supersample of this block is out of transit
 #pragma unroll 2
-        for (int j = 0; j + 1 < n_j; ++j) {
-            float4 c = coef[j];
-            float tj = Tn[j + 1];
+        for (int j = n_j - 1; j >= 0; --j) {
+            float4 c = tab[j];
 #pragma unroll
             for (int u = 0; u < SB; ++u) {
-                float gn = fmaf(fmaf(c.y, x[u], c.x), g[u], c.z * gp[u]);
-                gp[u] = g[u];
-                g[u] = gn;
-                sum[u] = fmaf(tj, gn, sum[u]);
+                float al = fmaf(c.y, x[u], c.x);
+                float t = fmaf(c.z, b2v[u], c.w);
+                float bj = fmaf(al, b1[u], t);
+                b2v[u] = b1[u];
+                b1[u] = bj;
             }
         }
 #pragma unroll
@@ -331,7 +336,7 @@ __device__ __forceinline__ void gim_unit(const float4 *coef, const float *Tn, in
                 float q2 = q * q;
                 float pw = q2 * q2;
                 for (int i = 0; i < n; ++i) pw *= q;
-                acc = fmaf(b2 * pw, sum[u], acc);
+                acc = fmaf(b2 * pw, b1[u], acc);
             }
         }
     }
@@ -351,10 +356,8 @@ __global__ void __launch_bounds__(TT) gim_lc_kernel(LcArgs A)
 
     const int NP1 = A.N + 1;
     const int nj = A.n_j;
-    const int tstride = NP1 * nj + 1;   // padded per-geometry stride of T
-    float4 *scoef = reinterpret_cast<float4 *>(dsm);                   // [NP1][nj]
-    float *sT = reinterpret_cast<float *>(scoef + NP1 * nj);          // [VT_G][tstride]
-    float *sacc = sT + VT_G * tstride;                                  // [VT_G][NP1][TT]
+    float4 *stab = reinterpret_cast<float4 *>(dsm);                    // [VT_G][NP1][nj]
+    float *sacc = reinterpret_cast<float *>(stab + VT_G * NP1 * nj);   // [VT_G][NP1][TT]
     float *sx = sacc + VT_G * NP1 * TT;                                 // [G_CHUNK][n_ss]
     float *sq = sx + G_CHUNK * A.n_ss;                                  // [G_CHUNK][n_ss]
 
@@ -365,12 +368,11 @@ __global__ void __launch_bounds__(TT) gim_lc_kernel(LcArgs A)
     const int nss = A.n_ss;
 
     if (qn > 0) {
-        for (int i = tl; i < NP1 * nj; i += TT) scoef[i] = A.gcoef[i];
         for (int vl = 0; vl < VT_G; ++vl) {
             int g = blockIdx.y * VT_G + vl;
             if (g >= A.n_geom) break;
-            const float *src = A.gT + (size_t)g * NP1 * nj;
-            for (int i = tl; i < NP1 * nj; i += TT) sT[vl * tstride + i] = src[i];
+            const float4 *src = A.gtab + (size_t)g * NP1 * nj;
+            for (int i = tl; i < NP1 * nj; i += TT) stab[vl * NP1 * nj + i] = src[i];
         }
     }
     __syncthreads();
@@ -406,8 +408,7 @@ __global__ void __launch_bounds__(TT) gim_lc_kernel(LcArgs A)
             float kk = srec[vl].k;
             float bb = kk / (1.0f + kk);
             float acc;
-            gim_unit<SB>(scoef + n * nj, sT + vl * tstride + n * nj, nj, n, bb * bb, sx + il * nss,
-                         sq + il * nss, nss, &acc);
+            gim_unit<SB>(stab + (vl * NP1 + n) * nj, nj, n, bb * bb, sx + il * nss, sq + il * nss, nss, &acc);
             sacc[(vl * NP1 + n) * TT + ti] = acc;
         }
         __syncthreads();
@@ -459,17 +460,18 @@ __global__ void __launch_bounds__(TT) gim_lc_kernel(LcArgs A)
 size_t gim_dyn_smem(int N, int n_j, int n_ss)
 {
     int NP1 = N + 1;
-    size_t b = (size_t)NP1 * n_j * sizeof(float4);
-    b += (size_t)VT_G * (NP1 * n_j + 1) * sizeof(float);
+    size_t b = (size_t)VT_G * NP1 * n_j * sizeof(float4);
     b += (size_t)VT_G * NP1 * TT * sizeof(float);
     b += (size_t)2 * G_CHUNK * n_ss * sizeof(float);
     return b;
 }
 
-// Gimenez per-geometry table T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2, FP64
-// recursion (coefficients from the plan), stored FP32.
+// Gimenez per-geometry table for Clenshaw's summation: entry (n, j) packs the
+// z-recursion coefficients r1_j, r2_j, r3_{j+1} of G_j(nu+2, 1; x) with
+// T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2, the z-independent factor of
+// Sec. 2.1.4 (FP64 recursion, stored FP32).
 __global__ void gim_table_kernel(const GeomRec *rec, int n_geom, int NP1, int n_j, const double *A,
-                                 const double *recb, float *T)
+                                 const double *recb, const float4 *coef, float4 *tab)
 {
     int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n_geom * NP1) return;
@@ -478,14 +480,16 @@ __global__ void gim_table_kernel(const GeomRec *rec, int n_geom, int NP1, int n_
     double x = 1.0 - k / (1.0 + k);
     const double *An = A + (size_t)n * n_j;
     const double *rb = recb + (size_t)n * n_j * 3;
-    float *Tg = T + ((size_t)g * NP1 + n) * n_j;
+    const float4 *cf = coef + (size_t)n * n_j;
+    float4 *out = tab + ((size_t)g * NP1 + n) * n_j;
     double gp = 0.0, gc = 1.0;
-    Tg[0] = (float)(An[0]);
-    for (int j = 0; j + 1 < n_j; ++j) {
+    for (int j = 0; j < n_j; ++j) {
+        float4 c = cf[j];
+        float r3n = (j + 1 < n_j) ? cf[j + 1].z : 0.0f;
+        out[j] = make_float4(c.x, c.y, r3n, (float)(An[j] * gc * gc));
         double gn = (rb[3 * j] + rb[3 * j + 1] * x) * gc + rb[3 * j + 2] * gp;
         gp = gc;
         gc = gn;
-        Tg[j + 1] = (float)(An[j + 1] * gc * gc);
     }
 }
 
@@ -651,7 +655,7 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
     L.tsplit = off;
     off += align256((size_t)n_t * sizeof(float2));
     L.T = off;
-    off += align256((size_t)n_geom * NP1 * n_j * sizeof(float));
+    off += align256((size_t)n_geom * NP1 * n_j * sizeof(float4));
     L.part = off;
     off += align256((size_t)n_v * n_b * n_tiles * sizeof(float));
     L.total = off;
@@ -971,13 +975,15 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
     char *wb = (char *)work;
     GeomRec *rec = (GeomRec *)(wb + L.rec);
     float2 *tsplit = (float2 *)(wb + L.tsplit);
-    float *T = (float *)(wb + L.T);
+    float4 *T = (float4 *)(wb + L.T);
     float *part = (float *)(wb + L.part);
     st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, s);
     if (st) return st;
     int n_geom = k_per_band ? orb->n_v * n_b : orb->n_v;
     int tot = n_geom * NP1;
-    gim_table_kernel<<<(tot + 63) / 64, 64, 0, s>>>(rec, n_geom, NP1, plan->n_j, plan->d_A, plan->d_recb, T);
+    // FP64 recursion chains: small blocks spread them over many SMs
+    gim_table_kernel<<<(tot + 15) / 16, 16, 0, s>>>(rec, n_geom, NP1, plan->n_j, plan->d_A, plan->d_recb,
+                                                   plan->d_coef, T);
     st = check_launch("gim_table_kernel");
     if (st) return st;
     LcArgs A;
@@ -1000,8 +1006,7 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
     A.ssr_part = ssr ? part : nullptr;
     A.n_tiles = (n_t + TT - 1) / TT;
     A.n_bad = n_bad;
-    A.gcoef = plan->d_coef;
-    A.gT = T;
+    A.gtab = T;
     A.N = plan->N;
     A.n_j = plan->n_j;
     int gy = (n_geom + VT_G - 1) / VT_G;
