@@ -135,13 +135,13 @@ def run_oracle_step(wl, n_v, n_t=None):
     return dt, fm.size + fg.size, (fm, fg)
 
 
-def bench_adjoint(pt, torch, dev, stream, K, flush):
+def bench_adjoint(pt, torch, dev, stream, K, flush, n_v=4096):
     """Adjoint workload: 4,096 eccentric vectors x 10,000 times, forward +
     gradient of the SSR w.r.t. 9 parameters per vector (pt_ma_quad_bwd).
     Reported in flux points (time x vector) per second, forward and backward
     together; y is a synthetic light curve (not timed)."""
     from paper_1504_07433_gb300 import workloads as W
-    wl = W.adjoint()
+    wl = W.adjoint(n_v=n_v)
     t = torch.as_tensor(wl["t"], dtype=torch.float64, device=dev)
     th = pt.theta_to_device(wl["theta"], dev)
     y = torch.ones(t.numel(), dtype=torch.float32, device=dev)
@@ -165,13 +165,13 @@ def bench_adjoint(pt, torch, dev, stream, K, flush):
             "gpu_launches_per_call": 2}
 
 
-def bench_batched(pt, torch, dev, stream, K, flush):
+def bench_batched(pt, torch, dev, stream, K, flush, n_walkers=1024, modes=("ssr", "cube")):
     """Batched spectrophotometry: 1,024 walkers x 64 passbands (own k and LD)
     x 32 light curves of 500-5,000 points, one graph-captured persistent
     launch per evaluation, autotuned.  Two modes: fused SSR (no flux cube)
     and the full FP32 flux cube (~23 GB written per evaluation)."""
     from paper_1504_07433_gb300 import workloads as W
-    wl = W.batched()
+    wl = W.batched(n_walkers=n_walkers)
     t = torch.as_tensor(wl["t"], dtype=torch.float64, device=dev)
     orb = pt.orbit_to_device(wl["orbit"], dev)
     k = torch.as_tensor(wl["k"], dtype=torch.float32, device=dev)
@@ -203,6 +203,8 @@ def bench_batched(pt, torch, dev, stream, K, flush):
     plan.close()
     del plan
     torch.cuda.empty_cache()
+    if "cube" not in modes:
+        return out
     plan = pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, want_flux=True, want_ssr=False, autotune=True)
     m = timed(plan)
     peaks, src = _peaks()
@@ -215,7 +217,7 @@ def bench_batched(pt, torch, dev, stream, K, flush):
     return out
 
 
-def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000):
+def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000, epochs=40):
     """Surrogate network: trained here on 1e7 exact-kernel samples (40 epochs,
     the library's own kernels), error-bound table from 4e6 validation points,
     then 1e9 band points through pt_ma_surrogate (BF16 tensor cores + exact
@@ -224,7 +226,7 @@ def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000):
     t0 = time.perf_counter()
     X, T, _ = S.datagen(10_000_000, seed=1504, device=dev)
     tr = S.Trainer(S.init_params(0, device=dev), batch=16384, device=dev)
-    tr.fit(X, T, epochs=40, lr0=1e-3, lr1=1e-6, qat_epochs=3)
+    tr.fit(X, T, epochs=epochs, lr0=1e-3, lr1=1e-6, qat_epochs=min(3, epochs))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del X, T
@@ -259,8 +261,8 @@ def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000):
             ms.append(e0.elapsed_time(e1))
         res[name] = float(np.mean(ms))
     share = 1.0 - int(nfb.item()) / n_infer
-    out = {"workload": "1e9 (k, z) points over k in [0.01, 0.3], z in [|1-k|, 1+k]",
-           "train_s": t_train, "train_samples": 10_000_000, "epochs": 40,
+    out = {"workload": "%.0e (k, z) points over k in [0.01, 0.3], z in [|1-k|, 1+k]" % n_infer,
+           "train_s": t_train, "train_samples": 10_000_000, "epochs": epochs,
            "table_cells_exact": float(table.mean()), "network_share": share,
            "exact_ms": res["exact"], "surrogate_ms": res["surrogate"],
            "exact_points_per_s": n_infer / (res["exact"] * 1e-3),
@@ -271,6 +273,28 @@ def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000):
     del k, z, outs, work
     torch.cuda.empty_cache()
     return out
+
+
+def only_main(args):
+    """One extra leg alone, at full or reduced size (profiler capture cases)."""
+    import torch
+    import paper_1504_07433_gb300 as pt
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    pt.load_library(build_if_missing=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    K = args.steps
+    if args.only == "adjoint":
+        out = bench_adjoint(pt, torch, dev, stream, K, flush, n_v=512 if args.small else 4096)
+    elif args.only == "batched":
+        out = bench_batched(pt, torch, dev, stream, K, flush, n_walkers=64 if args.small else 1024,
+                            modes=("ssr",) if args.small else ("ssr", "cube"))
+    else:
+        out = bench_surrogate(torch, dev, stream, n_infer=10_000_000 if args.small else 1_000_000_000,
+                              epochs=4 if args.small else 40)
+    print(json.dumps({"only": args.only, "small": bool(args.small), "result": out}), flush=True)
+    return 0
 
 
 def reference_main(args):
@@ -317,6 +341,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the adjoint / batched / surrogate legs")
     ap.add_argument("--n-v", type=int, default=256, help="parameter vectors (smaller only for profiler captures)")
     ap.add_argument("--n-t", type=int, default=50000, help="exposure times (smaller only for profiler captures)")
+    ap.add_argument("--only", default=None, choices=["adjoint", "batched", "surrogate"],
+                    help="run one extra leg alone (profiler captures); prints its JSON object")
+    ap.add_argument("--small", action="store_true", help="with --only: a reduced size for profiler captures")
     ap.add_argument("--heat-s", type=float, default=1.0,
                     help="seconds of extra untimed steps before the timed region, with the clock sampler running")
     args = ap.parse_args()
@@ -331,6 +358,8 @@ def main():
     import paper_1504_07433_gb300 as pt
     from paper_1504_07433_gb300 import workloads as W
 
+    if args.only:
+        return only_main(args)
     ws, rank, local = _dist()
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
