@@ -33,10 +33,8 @@ namespace {
 
 constexpr int TT = 256;      // times per CTA (= threads per CTA)
 constexpr int VT_MA = 8;     // geometries per CTA, Mandel-Agol
-constexpr int VT_G = 2;      // geometries per CTA, Gimenez
 constexpr int MAX_SS = 256;  // supersamples per exposure
 constexpr int MAX_NEWTON = 64;  // cap on Newton steps
-constexpr int G_CHUNK = 64;  // queued pairs per Gimenez evaluation round
 constexpr double PI_D = 3.14159265358979323846;
 
 thread_local char g_last_error[512] = "";
@@ -80,6 +78,7 @@ struct SetupArgs {
     const float *a, *inc, *e, *w, *k;
     int n_v, n_b, k_per_band, n_geom;
     GeomRec *rec;
+    int *cnt;            // per-geometry list counters to zero, or null
     float half_exp;
     int n_gblocks;
 };
@@ -95,7 +94,10 @@ __global__ void setup_kernel(SetupArgs s)
 {
     if ((int)blockIdx.x < s.n_gblocks) {
         int g = blockIdx.x * blockDim.x + threadIdx.x;
-        if (g < s.n_geom) make_geom(s, g, &s.rec[g]);
+        if (g < s.n_geom) {
+            make_geom(s, g, &s.rec[g]);
+            if (s.cnt) s.cnt[g] = 0;
+        }
     } else {
         int i = (blockIdx.x - s.n_gblocks) * blockDim.x + threadIdx.x;
         if (i < s.n_t) {
@@ -125,9 +127,6 @@ struct LcArgs {
     float *ssr_part;     // [rows][n_tiles]
     int n_tiles;
     int *n_bad;
-    // Gimenez
-    const float4 *gtab;  // [n_geom][N+1][n_j]: (r1_j, r2_j, r3_{j+1}, T_j)
-    int N, n_j;
 };
 
 __device__ __forceinline__ float block_sum(float v, float *sred)
@@ -285,150 +284,264 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 // ---------------------------------------------------------------------------
 // Gimenez light curves
 //
-// Per geometry the set-up pass stores T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2
-// (Sec. 2.1.4: the z-independent factors).  Per unit the kernel runs the
-// three-term recursion of G_j(nu+2, 1; c^2) and accumulates
+// Per geometry the table pass stores T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2
+// (Sec. 2.1.4: the z-independent factors).  Per (time, geometry) pair the
+// series kernel accumulates, for n = 0..N,
 //   alpha_n = b^2 (1 - c^2)^{nu+1} sum_j T_{n,j} G_j(nu+2, 1; c^2),
-// "only summations and multiplications" (Sec. 2.1.4).  Units are
-// (pair, n) so that a warp shares n (broadcast coefficient loads); each unit
-// carries all supersamples of its pair in registers, SB at a time.
+// with only summations and multiplications in the z-dependent part
+// (Sec. 2.1.4).  Three kernels:
+//   gim_window_kernel  every pair: window test; pairs in the window go to a
+//                      per-geometry list, the others get flux 1;
+//   gim_scan_kernel    work items per geometry (ppi listed pairs each) and
+//                      their exclusive prefix;
+//   gim_series_kernel  persistent CTAs take work items from an atomic
+//                      counter, stage the geometry's table once per item and
+//                      give each pair one thread (or two threads, each with
+//                      half of the supersamples).
+// Every pair's flux is computed by the same threads in the same order
+// whatever CTA takes its item, so the result is deterministic.
 // ---------------------------------------------------------------------------
-template <int SB>
-__device__ __forceinline__ void gim_unit(const float4 *tab, int n_j, int n, float b2, const float *sx,
-                                         const float *sq, int nss, float *acc_out)
+constexpr int GW_VT = 8;          // geometries per CTA of the window kernel
+constexpr int GS_THREADS = 128;   // threads per CTA of the series kernel
+constexpr int G_MAX_NP1 = 17;     // N <= 16
+
+struct GimArgs {
+    const float2 *tsplit;
+    int n_t;
+    const GeomRec *rec;
+    int n_geom;
+    const float4 *gtab;   // [n_geom][N+1][n_j]: (r1_j, r2_j, r3_{j+1}, T_j)
+    int N, n_j;
+    const float *ld;      // [rows][N]
+    int n_bpg;            // band rows per geometry
+    int n_ss;
+    float t_exp;
+    int max_iter;
+    float *flux;          // [rows][n_t]
+    int *cnt;             // [n_geom] listed pairs per geometry
+    int *pref;            // [n_geom + 1] work items before each geometry
+    int *ctr;             // next work item of the series kernel
+    int *list;            // [n_geom][n_t] time indices of listed pairs
+    int ppi;              // pairs per work item (GS_THREADS or GS_THREADS / 2)
+    int *n_bad;
+};
+
+__global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A)
 {
-    // Clenshaw's backward summation of S = sum_j T_j G_j with
-    // G_{j+1} = (r1_j + r2_j x) G_j + r3_j G_{j-1}, G_0 = 1, G_{-1} = 0:
-    //   b_j = T_j + (r1_j + r2_j x) b_{j+1} + r3_{j+1} b_{j+2},  S = b_0,
-    // three FMAs per term; tab[j] = (r1_j, r2_j, r3_{j+1}, T_j).
-    float acc = 0.0f;
+    __shared__ GeomRec srec[GW_VT];
+    const int tl = threadIdx.x;
+    for (int i = tl; i < GW_VT * 6; i += TT) {
+        int vl = i / 6, c = i % 6;
+        int g = blockIdx.y * GW_VT + vl;
+        if (g < A.n_geom)
+            reinterpret_cast<float4 *>(&srec[vl])[c] = reinterpret_cast<const float4 *>(&A.rec[g])[c];
+    }
+    __syncthreads();
+    const int t = blockIdx.x * TT + tl;
+    const bool tv = t < A.n_t;
+    const float2 ts = tv ? A.tsplit[t] : make_float2(0.0f, 0.0f);
 #pragma unroll 1
-    for (int s0 = 0; s0 < nss; s0 += SB) {
-        float x[SB], b1[SB], b2v[SB];
+    for (int vl = 0; vl < GW_VT; ++vl) {
+        int g = blockIdx.y * GW_VT + vl;
+        if (g >= A.n_geom) break;   // uniform over the CTA
+        bool inw = false;
+        if (tv) {
+            float dt = pt::reduce_time(ts.x, ts.y, srec[vl]);
+            inw = (dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi);
+        }
+        int slot = pt::warp_append(A.cnt + g, inw);
+        if (inw) {
+            A.list[(size_t)g * A.n_t + slot] = t;
+        } else if (tv) {
+            for (int bb = 0; bb < A.n_bpg; ++bb) A.flux[((size_t)g * A.n_bpg + bb) * A.n_t + t] = 1.0f;
+        }
+    }
+}
+
+// pref[g] = sum over g' < g of ceil(cnt[g'] / ppi); pref[n_geom] = total.
+// One CTA of 1024 threads; also rewinds the series kernel's item counter.
+__global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_geom, int ppi, int *pref, int *ctr)
+{
+    __shared__ int swarp[32];
+    __shared__ int scarry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        scarry = 0;
+        *ctr = 0;
+    }
+    __syncthreads();
+    for (int base = 0; base < n_geom; base += blockDim.x) {
+        int g = base + threadIdx.x;
+        int v = (g < n_geom) ? (cnt[g] + ppi - 1) / ppi : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) swarp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = (lane < nwarp) ? swarp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            swarp[lane] = w;
+        }
+        __syncthreads();
+        int incl = scarry + (warp > 0 ? swarp[warp - 1] : 0) + x;
+        if (g < n_geom) pref[g] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) scarry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pref[n_geom] = scarry;
+}
+
+// One thread's share of a pair: supersamples [s_lo, s_hi), SB at a time.
+// For each block the supersamples' z give x = c^2 and q = sqrt(1 - c^2)
+// (c = z / (1 + k)); then for every n Clenshaw's backward summation of
+// S = sum_j T_j G_j with G_{j+1} = (r1_j + r2_j x) G_j + r3_j G_{j-1},
+// G_0 = 1, G_{-1} = 0:
+//   b_j = T_j + (r1_j + r2_j x) b_{j+1} + r3_{j+1} b_{j+2},  S = b_0,
+// three FMAs per term; (1 - c^2)^{nu+1} = q^4 q^n with nu = (n+2)/2.
+// The partial alpha_n go to salpha[n] (this thread's column).
+template <int SB>
+__device__ __forceinline__ void gim_pair(const float4 *stab, int NP1, int n_j, const GeomRec &r, float dt,
+                                         float t_exp, int nss, int s_lo, int s_hi, int max_iter,
+                                         float (*salpha)[GS_THREADS], int col, int *nbad)
+{
+    const float kk = r.k;
+    const float bk = kk / (1.0f + kk);
+    const float b2 = bk * bk;
+#pragma unroll 1
+    for (int s0 = s_lo; s0 < s_hi; s0 += SB) {
+        float x[SB], q[SB];
         bool any = false;
 #pragma unroll
         for (int u = 0; u < SB; ++u) {
             int s = s0 + u;
-            x[u] = (s < nss) ? sx[s] : 0.0f;
-            any |= (s < nss) && (sq[s] > 0.0f);
-            b1[u] = 0.0f;
-            b2v[u] = 0.0f;
+            x[u] = 0.0f;
+            q[u] = 0.0f;
+            if (s < s_hi) {
+                bool bad = false;
+                float z = pt::orbit_z(r, dt + ss_offset(t_exp, s, nss), max_iter, &bad);
+                if (bad) ++*nbad;
+                if (z < 1.0f + kk) {
+                    float c = z / (1.0f + kk);
+                    x[u] = c * c;
+                    q[u] = sqrtf((1.0f - c) * (1.0f + c));
+                }
+            }
+            any |= q[u] > 0.0f;
         }
         if (!any) continue;   // every supersample of this block is out of transit
-#pragma unroll 2
-        for (int j = n_j - 1; j >= 0; --j) {
-            float4 c = tab[j];
+#pragma unroll 1
+        for (int n = 0; n < NP1; ++n) {
+            const float4 *tab = stab + n * n_j;
+            float b1[SB], b2v[SB];
 #pragma unroll
             for (int u = 0; u < SB; ++u) {
-                float al = fmaf(c.y, x[u], c.x);
-                float t = fmaf(c.z, b2v[u], c.w);
-                float bj = fmaf(al, b1[u], t);
-                b2v[u] = b1[u];
-                b1[u] = bj;
+                b1[u] = 0.0f;
+                b2v[u] = 0.0f;
             }
-        }
+#pragma unroll 8
+            for (int j = n_j - 1; j >= 0; --j) {
+                float4 c = tab[j];
 #pragma unroll
-        for (int u = 0; u < SB; ++u) {
-            int s = s0 + u;
-            if (s < nss) {
-                // (1 - c^2)^{nu+1} = (1 - c^2)^2 sqrt(1 - c^2)^n, nu = (n+2)/2
-                float q = sq[s];
-                float q2 = q * q;
-                float pw = q2 * q2;
-                for (int i = 0; i < n; ++i) pw *= q;
+                for (int u = 0; u < SB; ++u) {
+                    float al = fmaf(c.y, x[u], c.x);
+                    float t = fmaf(c.z, b2v[u], c.w);
+                    float bj = fmaf(al, b1[u], t);
+                    b2v[u] = b1[u];
+                    b1[u] = bj;
+                }
+            }
+            float acc = 0.0f;
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+                float qq = q[u] * q[u];
+                float pw = qq * qq;
+                for (int i = 0; i < n; ++i) pw *= q[u];
                 acc = fmaf(b2 * pw, b1[u], acc);
             }
+            salpha[n][col] += acc;
         }
     }
-    *acc_out = acc;
 }
 
 template <int SB>
-__global__ void __launch_bounds__(TT) gim_lc_kernel(LcArgs A)
+__global__ void __launch_bounds__(GS_THREADS) gim_series_kernel(GimArgs A)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ GeomRec srec[VT_G];
-    __shared__ float sdt[VT_G][TT];
-    __shared__ unsigned char sflag[VT_G][TT];
-    __shared__ unsigned short squeue[VT_G * TT];
-    __shared__ float sred[TT / 32];
-    __shared__ int sqn, sbad;
+    float4 *stab = reinterpret_cast<float4 *>(dsm);   // [N+1][n_j]
+    __shared__ GeomRec srec;
+    __shared__ float salpha[G_MAX_NP1][GS_THREADS];
+    __shared__ int sitem, sgeom, sbad;
 
     const int NP1 = A.N + 1;
     const int nj = A.n_j;
-    float4 *stab = reinterpret_cast<float4 *>(dsm);                    // [VT_G][NP1][nj]
-    float *sacc = reinterpret_cast<float *>(stab + VT_G * NP1 * nj);   // [VT_G][NP1][TT]
-    float *sx = sacc + VT_G * NP1 * TT;                                 // [G_CHUNK][n_ss]
-    float *sq = sx + G_CHUNK * A.n_ss;                                  // [G_CHUNK][n_ss]
-
-    if (threadIdx.x == 0) sbad = 0;
-    phase_a<VT_G>(A, srec, sdt, sflag, squeue, &sqn);
-    const int tl = threadIdx.x;
-    const int qn = sqn;
     const int nss = A.n_ss;
-
-    if (qn > 0) {
-        for (int vl = 0; vl < VT_G; ++vl) {
-            int g = blockIdx.y * VT_G + vl;
-            if (g >= A.n_geom) break;
-            const float4 *src = A.gtab + (size_t)g * NP1 * nj;
-            for (int i = tl; i < NP1 * nj; i += TT) stab[vl * NP1 * nj + i] = src[i];
-        }
-    }
-    __syncthreads();
-
-#pragma unroll 1
-    for (int base = 0; base < qn; base += G_CHUNK) {
-        int nit = min(G_CHUNK, qn - base);
-        // B1: z of every (pair, supersample) of the chunk
-        for (int u = tl; u < nit * nss; u += TT) {
-            int il = u / nss, s = u - il * nss;
-            int code = squeue[base + il];
-            int vl = code / TT, ti = code % TT;
-            const GeomRec &r = srec[vl];
-            float dts = sdt[vl][ti] + ss_offset(A.t_exp, s, nss);
-            bool bad = false;
-            float z = pt::orbit_z(r, dts, A.max_iter, &bad);
-            if (bad) atomicAdd(&sbad, 1);
-            float xv = 0.0f, qv = 0.0f;
-            if (z < 1.0f + r.k) {
-                float c = z / (1.0f + r.k);
-                xv = c * c;
-                qv = sqrtf((1.0f - c) * (1.0f + c));
-            }
-            sx[u] = xv;
-            sq[u] = qv;
-        }
-        __syncthreads();
-        // B2: (pair, n) units
-        for (int u = tl; u < nit * NP1; u += TT) {
-            int n = u / nit, il = u - n * nit;
-            int code = squeue[base + il];
-            int vl = code / TT, ti = code % TT;
-            float kk = srec[vl].k;
-            float bb = kk / (1.0f + kk);
-            float acc;
-            gim_unit<SB>(stab + (vl * NP1 + n) * nj, nj, n, bb * bb, sx + il * nss, sq + il * nss, nss, &acc);
-            sacc[(vl * NP1 + n) * TT + ti] = acc;
-        }
-        __syncthreads();
-    }
-
-    // Phase C
-    const int t = blockIdx.x * TT + tl;
-    const bool tv = t < A.n_t;
+    const int ppi = A.ppi;
+    const int tid = threadIdx.x;
+    const bool split = ppi < GS_THREADS;   // two threads per pair
+    const int half = split ? tid / ppi : 0;
+    const int pl = tid - half * ppi;
+    const int s_mid = (nss + 1) / 2;
+    const int s_lo = (split && half) ? s_mid : 0;
+    const int s_hi = (split && !half) ? s_mid : nss;
+    const int total = A.pref[A.n_geom];
     const float inv_nss = 1.0f / (float)nss;
+    int nbad = 0;
+    int staged = -1;
+    if (tid == 0) sbad = 0;
+
 #pragma unroll 1
-    for (int vl = 0; vl < VT_G; ++vl) {
-        int g = blockIdx.y * VT_G + vl;
-        if (g >= A.n_geom) break;
-        bool inw = tv && sflag[vl][tl];
+    for (;;) {
+        if (tid == 0) {
+            int it = atomicAdd(A.ctr, 1);
+            int g = -1;
+            if (it < total) {   // the largest g with pref[g] <= it
+                int lo = 0, hi = A.n_geom - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (A.pref[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                g = lo;
+            }
+            sitem = it;
+            sgeom = g;
+        }
+        __syncthreads();
+        const int it = sitem;
+        const int g = sgeom;
+        if (it >= total) break;   // uniform over the CTA
+        if (g != staged) {
+            const float4 *src = A.gtab + (size_t)g * NP1 * nj;
+            for (int i = tid; i < NP1 * nj; i += GS_THREADS) stab[i] = src[i];
+            if (tid < 6) reinterpret_cast<float4 *>(&srec)[tid] = reinterpret_cast<const float4 *>(&A.rec[g])[tid];
+            staged = g;
+        }
+        for (int n = 0; n < NP1; ++n) salpha[n][tid] = 0.0f;
+        __syncthreads();
+        const int i = (it - A.pref[g]) * ppi + pl;
+        const bool valid = i < A.cnt[g];
+        const int t = valid ? A.list[(size_t)g * A.n_t + i] : 0;
+        if (valid && s_lo < s_hi) {
+            float2 ts = A.tsplit[t];
+            float dt = pt::reduce_time(ts.x, ts.y, srec);
+            gim_pair<SB>(stab, NP1, nj, srec, dt, A.t_exp, nss, s_lo, s_hi, A.max_iter, salpha, tid, &nbad);
+        }
+        __syncthreads();
+        if (valid && half == 0) {
 #pragma unroll 1
-        for (int bb = 0; bb < A.n_bpg; ++bb) {
-            int row = g * A.n_bpg + bb;
-            const float *u = A.ld + (size_t)row * A.N;
-            float f = 1.0f;
-            if (inw) {
+            for (int bb = 0; bb < A.n_bpg; ++bb) {
+                size_t row = (size_t)g * A.n_bpg + bb;
+                const float *u = A.ld + row * A.N;
                 // C_0 = (1 - sum u)/D, C_n = u_n/D, D = 1 - sum n u_n/(n+2)   (Sec. 2.1.3)
                 float su = 0.0f, sd = 0.0f;
                 for (int n = 1; n <= A.N; ++n) {
@@ -436,35 +549,22 @@ __global__ void __launch_bounds__(TT) gim_lc_kernel(LcArgs A)
                     su += un;
                     sd += (float)n * un / (float)(n + 2);
                 }
-                float invD = 1.0f / (1.0f - sd);
-                float al = (1.0f - su) * sacc[(vl * NP1 + 0) * TT + tl];
-                for (int n = 1; n <= A.N; ++n) al = fmaf(u[n - 1], sacc[(vl * NP1 + n) * TT + tl], al);
-                f = 1.0f - al * invD * inv_nss;
-            }
-            if (A.flux && tv) A.flux[(size_t)row * A.n_t + t] = f;
-            if (A.ssr_part) {
-                int band = A.k_per_band ? (g % A.n_b) : bb;
-                float val = 0.0f;
-                if (tv) {
-                    float r = A.y[(size_t)band * A.n_t + t] - f;
-                    val = (A.wt ? A.wt[(size_t)band * A.n_t + t] : 1.0f) * r * r;
+                float a0 = salpha[0][pl] + (split ? salpha[0][pl + ppi] : 0.0f);
+                float al = (1.0f - su) * a0;
+                for (int n = 1; n <= A.N; ++n) {
+                    float an = salpha[n][pl] + (split ? salpha[n][pl + ppi] : 0.0f);
+                    al = fmaf(u[n - 1], an, al);
                 }
-                float tot = block_sum(val, sred);
-                if (tl == 0) A.ssr_part[(size_t)row * A.n_tiles + blockIdx.x] = tot;
+                A.flux[row * A.n_t + t] = 1.0f - al / (1.0f - sd) * inv_nss;
             }
         }
     }
-    if (tl == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
+    if (nbad) atomicAdd(&sbad, nbad);
+    __syncthreads();
+    if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
 }
 
-size_t gim_dyn_smem(int N, int n_j, int n_ss)
-{
-    int NP1 = N + 1;
-    size_t b = (size_t)VT_G * NP1 * n_j * sizeof(float4);
-    b += (size_t)VT_G * NP1 * TT * sizeof(float);
-    b += (size_t)2 * G_CHUNK * n_ss * sizeof(float);
-    return b;
-}
+size_t gim_series_smem(int N, int n_j) { return (size_t)(N + 1) * n_j * sizeof(float4); }
 
 // Gimenez per-geometry table for Clenshaw's summation: entry (n, j) packs the
 // z-recursion coefficients r1_j, r2_j, r3_{j+1} of G_j(nu+2, 1; x) with
@@ -503,6 +603,26 @@ __global__ void ssr_reduce_kernel(const float *part, int rows, int n_tiles, floa
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) ssr[warp] = s;
+}
+
+// ssr[row] = sum_t wt (y - flux)^2 over one flux row, in a fixed order;
+// row r observes passband r % n_b (rows are geometry-major, band-minor).
+__global__ void __launch_bounds__(256) ssr_rows_kernel(const float *flux, const float *y, const float *wt,
+                                                      int n_t, int n_b, float *ssr)
+{
+    __shared__ float sred[8];
+    const size_t row = blockIdx.x;
+    const int band = (int)(row % n_b);
+    const float *f = flux + row * n_t;
+    const float *yb = y + (size_t)band * n_t;
+    const float *wb = wt ? wt + (size_t)band * n_t : nullptr;
+    float s = 0.0f;
+    for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
+        float r = yb[t] - f[t];
+        s = fmaf(wb ? wb[t] : 1.0f, r * r, s);
+    }
+    float tot = block_sum(s, sred);
+    if (threadIdx.x == 0) ssr[row] = tot;
 }
 
 // ---------------------------------------------------------------------------
@@ -640,8 +760,12 @@ int check_orbit(const pt_orbit *orb, bool need_ecc)
     return PT_OK;
 }
 
+// Mandel-Agol (NP1 == 0): records, time split, per-tile residual partials.
+// Gimenez: records, time split, per-geometry tables, list counters (+ the
+// work-item counter), work-item prefix, pair lists and a flux scratch used
+// when only residuals are asked for.
 struct WorkLayout {
-    size_t rec, tsplit, T, part, total;
+    size_t rec, tsplit, T, part, cnt, pref, list, fscr, total;
 };
 
 WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n_j)
@@ -654,10 +778,22 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
     off += align256((size_t)n_geom * sizeof(GeomRec));
     L.tsplit = off;
     off += align256((size_t)n_t * sizeof(float2));
-    L.T = off;
-    off += align256((size_t)n_geom * NP1 * n_j * sizeof(float4));
-    L.part = off;
-    off += align256((size_t)n_v * n_b * n_tiles * sizeof(float));
+    L.T = L.part = L.cnt = L.pref = L.list = L.fscr = off;
+    if (NP1 == 0) {
+        L.part = off;
+        off += align256((size_t)n_v * n_b * n_tiles * sizeof(float));
+    } else {
+        L.T = off;
+        off += align256((size_t)n_geom * NP1 * n_j * sizeof(float4));
+        L.cnt = off;
+        off += align256((size_t)(n_geom + 1) * sizeof(int));
+        L.pref = off;
+        off += align256((size_t)(n_geom + 1) * sizeof(int));
+        L.list = off;
+        off += align256((size_t)n_geom * n_t * sizeof(int));
+        L.fscr = off;
+        off += align256((size_t)n_v * n_b * n_t * sizeof(float));
+    }
     L.total = off;
     return L;
 }
@@ -702,18 +838,30 @@ void jacobi_rec(double p, double q, int j, double *r)
 }  // namespace
 
 namespace {
+// Persistent launch of the series kernel: as many CTAs as fit on the GPU at
+// once (never more than there can be work items).
 template <int SB>
-int launch_gim(const LcArgs &A, dim3 grid, size_t smem, cudaStream_t s)
+int launch_series(const GimArgs &A, size_t smem, size_t max_items, cudaStream_t s)
 {
     static thread_local size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(gim_lc_kernel<SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(gim_series_kernel<SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
-        if (e != cudaSuccess) return set_cuda_error(e, "gim_lc_kernel smem attribute");
+        if (e != cudaSuccess) return set_cuda_error(e, "gim_series_kernel smem attribute");
         configured = smem;
     }
-    gim_lc_kernel<SB><<<grid, TT, smem, s>>>(A);
-    return check_launch("gim_lc_kernel");
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gim_series_kernel<SB>, GS_THREADS, smem);
+    if (e != cudaSuccess) return set_cuda_error(e, "gim_series_kernel occupancy");
+    if (per_sm < 1) return pt_internal::set_error(PT_ERR_ARG, "gim_series_kernel", "does not fit on an SM");
+    size_t grid = (size_t)n_sm * per_sm;
+    if (grid > max_items) grid = max_items;
+    if (grid < 1) grid = 1;
+    gim_series_kernel<SB><<<(unsigned)grid, GS_THREADS, smem, s>>>(A);
+    return check_launch("gim_series_kernel");
 }
 
 }  // namespace
@@ -803,7 +951,7 @@ size_t pt_ma_quad_work_bytes(int n_t, int n_v, int n_b, int k_per_band)
 }
 
 static int launch_setup(const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band, int n_b,
-                        double t_exp, GeomRec *rec, float2 *tsplit, cudaStream_t s)
+                        double t_exp, GeomRec *rec, float2 *tsplit, int *cnt, cudaStream_t s)
 {
     SetupArgs sa;
     sa.t = t;
@@ -821,6 +969,7 @@ static int launch_setup(const double *t, int n_t, const pt_orbit *orb, const flo
     sa.k_per_band = k_per_band;
     sa.n_geom = k_per_band ? orb->n_v * n_b : orb->n_v;
     sa.rec = rec;
+    sa.cnt = cnt;
     sa.half_exp = (float)(0.5 * t_exp);
     const int bs = 64;
     sa.n_gblocks = (sa.n_geom + bs - 1) / bs;
@@ -843,7 +992,7 @@ int pt_ma_quad(const double *t, int n_t, const pt_orbit *orb, const float *k, in
     GeomRec *rec = (GeomRec *)(wb + L.rec);
     float2 *tsplit = (float2 *)(wb + L.tsplit);
     float *part = (float *)(wb + L.part);
-    st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, s);
+    st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, nullptr, s);
     if (st) return st;
     LcArgs A;
     memset(&A, 0, sizeof(A));
@@ -966,67 +1115,79 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
     int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, max_iter, y, flux, ssr, work);
     if (st) return st;
     if (n_t == 0 || orb->n_v == 0) return PT_OK;
-    int NP1 = plan->N + 1;
+    const int NP1 = plan->N + 1;
     WorkLayout L = work_layout(n_t, orb->n_v, n_b, k_per_band, NP1, plan->n_j);
     if (work_bytes < L.total) return PT_ERR_WORKSPACE;
-    size_t smem = gim_dyn_smem(plan->N, plan->n_j, n_ss);
+    const size_t smem = gim_series_smem(plan->N, plan->n_j);
     if (smem > 200 * 1024) return PT_ERR_ARG;
+    const int n_geom = k_per_band ? orb->n_v * n_b : orb->n_v;
+    const int n_tiles = (n_t + TT - 1) / TT;
+    const int gy = (n_geom + GW_VT - 1) / GW_VT;
+    if (gy > 65535) return PT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     char *wb = (char *)work;
     GeomRec *rec = (GeomRec *)(wb + L.rec);
     float2 *tsplit = (float2 *)(wb + L.tsplit);
     float4 *T = (float4 *)(wb + L.T);
-    float *part = (float *)(wb + L.part);
-    st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, s);
+    int *cnt = (int *)(wb + L.cnt);
+    st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, cnt, s);
     if (st) return st;
-    int n_geom = k_per_band ? orb->n_v * n_b : orb->n_v;
-    int tot = n_geom * NP1;
+    const int tot = n_geom * NP1;
     // FP64 recursion chains: small blocks spread them over many SMs
     gim_table_kernel<<<(tot + 15) / 16, 16, 0, s>>>(rec, n_geom, NP1, plan->n_j, plan->d_A, plan->d_recb,
                                                    plan->d_coef, T);
     st = check_launch("gim_table_kernel");
     if (st) return st;
-    LcArgs A;
+    GimArgs A;
     memset(&A, 0, sizeof(A));
     A.tsplit = tsplit;
     A.n_t = n_t;
     A.rec = rec;
     A.n_geom = n_geom;
+    A.gtab = T;
+    A.N = plan->N;
+    A.n_j = plan->n_j;
     A.ld = ld;
-    A.n_ld = plan->N;
-    A.n_b = n_b;
-    A.k_per_band = k_per_band;
     A.n_bpg = k_per_band ? 1 : n_b;
     A.n_ss = n_ss;
     A.t_exp = (float)t_exp;
     A.max_iter = max_iter;
-    A.y = y;
-    A.wt = wt;
-    A.flux = flux;
-    A.ssr_part = ssr ? part : nullptr;
-    A.n_tiles = (n_t + TT - 1) / TT;
+    A.flux = flux ? flux : (float *)(wb + L.fscr);
+    A.cnt = cnt;
+    A.pref = (int *)(wb + L.pref);
+    A.ctr = cnt + n_geom;
+    A.list = (int *)(wb + L.list);
+    A.ppi = (n_ss >= 2) ? GS_THREADS / 2 : GS_THREADS;
     A.n_bad = n_bad;
-    A.gtab = T;
-    A.N = plan->N;
-    A.n_j = plan->n_j;
-    int gy = (n_geom + VT_G - 1) / VT_G;
-    if (gy > 65535) return PT_ERR_ARG;
-    dim3 grid(A.n_tiles, gy);
-    if (n_ss % 5 == 0)
-        st = launch_gim<5>(A, grid, smem, s);
-    else if (n_ss % 4 == 0)
-        st = launch_gim<4>(A, grid, smem, s);
-    else if (n_ss % 2 == 0)
-        st = launch_gim<2>(A, grid, smem, s);
-    else if (n_ss == 1)
-        st = launch_gim<1>(A, grid, smem, s);
-    else
-        st = launch_gim<4>(A, grid, smem, s);
+    gim_window_kernel<<<dim3(n_tiles, gy), TT, 0, s>>>(A);
+    st = check_launch("gim_window_kernel");
+    if (st) return st;
+    gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, A.ppi, A.pref, A.ctr);
+    st = check_launch("gim_scan_kernel");
+    if (st) return st;
+    // supersamples per thread: h = n_ss split over the pair's threads,
+    // taken SB at a time (the last block of a ragged h is masked)
+    const int h = (A.ppi < GS_THREADS) ? (n_ss + 1) / 2 : n_ss;
+    const size_t max_items = (size_t)n_geom * ((n_t + A.ppi - 1) / A.ppi);
+    if (h <= 5) {
+        switch (h) {
+        case 1: st = launch_series<1>(A, smem, max_items, s); break;
+        case 2: st = launch_series<2>(A, smem, max_items, s); break;
+        case 3: st = launch_series<3>(A, smem, max_items, s); break;
+        case 4: st = launch_series<4>(A, smem, max_items, s); break;
+        default: st = launch_series<5>(A, smem, max_items, s); break;
+        }
+    } else if (h % 5 == 0) {
+        st = launch_series<5>(A, smem, max_items, s);
+    } else if (h % 3 == 0) {
+        st = launch_series<3>(A, smem, max_items, s);
+    } else {
+        st = launch_series<4>(A, smem, max_items, s);
+    }
     if (st) return st;
     if (ssr) {
-        int rows = orb->n_v * n_b;
-        ssr_reduce_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(part, rows, A.n_tiles, ssr);
-        st = check_launch("ssr_reduce_kernel");
+        ssr_rows_kernel<<<orb->n_v * n_b, 256, 0, s>>>(A.flux, y, wt, n_t, n_b, ssr);
+        st = check_launch("ssr_rows_kernel");
     }
     return st;
 }
