@@ -296,13 +296,14 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 //                      their exclusive prefix;
 //   gim_series_kernel  persistent CTAs take work items from an atomic
 //                      counter, stage the geometry's table once per item and
-//                      give each pair one thread (or two threads, each with
-//                      half of the supersamples).
+//                      give each pair one thread (two threads, each with
+//                      half of the supersamples, for long supersample lists).
 // Every pair's flux is computed by the same threads in the same order
 // whatever CTA takes its item, so the result is deterministic.
 // ---------------------------------------------------------------------------
 constexpr int GW_VT = 8;          // geometries per CTA of the window kernel
 constexpr int GS_THREADS = 128;   // threads per CTA of the series kernel
+constexpr int GS_MIN_CTAS = 6;    // resident CTAs per SM the register budget is sized for
 constexpr int G_MAX_NP1 = 17;     // N <= 16
 
 struct GimArgs {
@@ -326,9 +327,12 @@ struct GimArgs {
     int *n_bad;
 };
 
+// Pairs are counted per CTA in shared memory first, then one global atomic
+// per geometry reserves the CTA's stretch of that geometry's list.
 __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A)
 {
     __shared__ GeomRec srec[GW_VT];
+    __shared__ int scount[GW_VT], sbase[GW_VT];
     const int tl = threadIdx.x;
     for (int i = tl; i < GW_VT * 6; i += TT) {
         int vl = i / 6, c = i % 6;
@@ -336,22 +340,33 @@ __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A)
         if (g < A.n_geom)
             reinterpret_cast<float4 *>(&srec[vl])[c] = reinterpret_cast<const float4 *>(&A.rec[g])[c];
     }
+    if (tl < GW_VT) scount[tl] = 0;
     __syncthreads();
     const int t = blockIdx.x * TT + tl;
     const bool tv = t < A.n_t;
     const float2 ts = tv ? A.tsplit[t] : make_float2(0.0f, 0.0f);
-#pragma unroll 1
+    const int g0 = blockIdx.y * GW_VT;
+    int slot[GW_VT];
+    unsigned inw_bits = 0u;
+#pragma unroll
     for (int vl = 0; vl < GW_VT; ++vl) {
-        int g = blockIdx.y * GW_VT + vl;
-        if (g >= A.n_geom) break;   // uniform over the CTA
         bool inw = false;
-        if (tv) {
+        if (tv && g0 + vl < A.n_geom) {
             float dt = pt::reduce_time(ts.x, ts.y, srec[vl]);
             inw = (dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi);
         }
-        int slot = pt::warp_append(A.cnt + g, inw);
-        if (inw) {
-            A.list[(size_t)g * A.n_t + slot] = t;
+        slot[vl] = pt::warp_append(&scount[vl], inw);
+        if (inw) inw_bits |= 1u << vl;
+    }
+    __syncthreads();
+    if (tl < GW_VT) sbase[tl] = (scount[tl] > 0) ? atomicAdd(A.cnt + g0 + tl, scount[tl]) : 0;
+    __syncthreads();
+#pragma unroll
+    for (int vl = 0; vl < GW_VT; ++vl) {
+        const int g = g0 + vl;
+        if (g >= A.n_geom) break;   // uniform over the CTA
+        if (inw_bits & (1u << vl)) {
+            A.list[(size_t)g * A.n_t + sbase[vl] + slot[vl]] = t;
         } else if (tv) {
             for (int bb = 0; bb < A.n_bpg; ++bb) A.flux[((size_t)g * A.n_bpg + bb) * A.n_t + t] = 1.0f;
         }
@@ -401,14 +416,38 @@ __global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_ge
     if (threadIdx.x == 0) pref[n_geom] = scarry;
 }
 
+// Two-lane FP32 arithmetic (sm_100 family): a 64-bit register holds two
+// floats and one fma.rn.f32x2 performs both lanes' FMAs, each rounded like
+// fmaf.  Two supersamples of a pair ride in the two lanes.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_split(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // One thread's share of a pair: supersamples [s_lo, s_hi), SB at a time.
 // For each block the supersamples' z give x = c^2 and q = sqrt(1 - c^2)
 // (c = z / (1 + k)); then for every n Clenshaw's backward summation of
 // S = sum_j T_j G_j with G_{j+1} = (r1_j + r2_j x) G_j + r3_j G_{j-1},
 // G_0 = 1, G_{-1} = 0:
 //   b_j = T_j + (r1_j + r2_j x) b_{j+1} + r3_{j+1} b_{j+2},  S = b_0,
-// three FMAs per term; (1 - c^2)^{nu+1} = q^4 q^n with nu = (n+2)/2.
-// The partial alpha_n go to salpha[n] (this thread's column).
+// three FMAs per term and supersample, two supersamples per two-lane FMA
+// when SB is even; (1 - c^2)^{nu+1} = q^4 q^n with nu = (n+2)/2.  The
+// partial alpha_n go to salpha[n] (this thread's column).
 template <int SB>
 __device__ __forceinline__ void gim_pair(const float4 *stab, int NP1, int n_j, const GeomRec &r, float dt,
                                          float t_exp, int nss, int s_lo, int s_hi, int max_iter,
@@ -443,21 +482,47 @@ __device__ __forceinline__ void gim_pair(const float4 *stab, int NP1, int n_j, c
         for (int n = 0; n < NP1; ++n) {
             const float4 *tab = stab + n * n_j;
             float b1[SB], b2v[SB];
+            if constexpr (SB % 2 == 0) {
+                unsigned long long xp[SB / 2], bp1[SB / 2], bp2[SB / 2];
 #pragma unroll
-            for (int u = 0; u < SB; ++u) {
-                b1[u] = 0.0f;
-                b2v[u] = 0.0f;
-            }
+                for (int p = 0; p < SB / 2; ++p) {
+                    xp[p] = f2_pack(x[2 * p], x[2 * p + 1]);
+                    bp1[p] = 0ull;
+                    bp2[p] = 0ull;
+                }
 #pragma unroll 8
-            for (int j = n_j - 1; j >= 0; --j) {
-                float4 c = tab[j];
+                for (int j = n_j - 1; j >= 0; --j) {
+                    float4 c = tab[j];
+                    unsigned long long cx = f2_pack(c.x, c.x), cy = f2_pack(c.y, c.y);
+                    unsigned long long cz = f2_pack(c.z, c.z), cw = f2_pack(c.w, c.w);
+#pragma unroll
+                    for (int p = 0; p < SB / 2; ++p) {
+                        unsigned long long al = f2_fma(cy, xp[p], cx);
+                        unsigned long long t = f2_fma(cz, bp2[p], cw);
+                        unsigned long long bj = f2_fma(al, bp1[p], t);
+                        bp2[p] = bp1[p];
+                        bp1[p] = bj;
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < SB / 2; ++p) f2_split(bp1[p], b1[2 * p], b1[2 * p + 1]);
+            } else {
 #pragma unroll
                 for (int u = 0; u < SB; ++u) {
-                    float al = fmaf(c.y, x[u], c.x);
-                    float t = fmaf(c.z, b2v[u], c.w);
-                    float bj = fmaf(al, b1[u], t);
-                    b2v[u] = b1[u];
-                    b1[u] = bj;
+                    b1[u] = 0.0f;
+                    b2v[u] = 0.0f;
+                }
+#pragma unroll 8
+                for (int j = n_j - 1; j >= 0; --j) {
+                    float4 c = tab[j];
+#pragma unroll
+                    for (int u = 0; u < SB; ++u) {
+                        float al = fmaf(c.y, x[u], c.x);
+                        float t = fmaf(c.z, b2v[u], c.w);
+                        float bj = fmaf(al, b1[u], t);
+                        b2v[u] = b1[u];
+                        b1[u] = bj;
+                    }
                 }
             }
             float acc = 0.0f;
@@ -474,7 +539,7 @@ __device__ __forceinline__ void gim_pair(const float4 *stab, int NP1, int n_j, c
 }
 
 template <int SB>
-__global__ void __launch_bounds__(GS_THREADS) gim_series_kernel(GimArgs A)
+__global__ void __launch_bounds__(GS_THREADS, GS_MIN_CTAS) gim_series_kernel(GimArgs A)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *stab = reinterpret_cast<float4 *>(dsm);   // [N+1][n_j]
@@ -570,28 +635,44 @@ size_t gim_series_smem(int N, int n_j) { return (size_t)(N + 1) * n_j * sizeof(f
 // z-recursion coefficients r1_j, r2_j, r3_{j+1} of G_j(nu+2, 1; x) with
 // T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2, the z-independent factor of
 // Sec. 2.1.4 (FP64 recursion, stored FP32).
-__global__ void gim_table_kernel(const GeomRec *rec, int n_geom, int NP1, int n_j, const double *A,
-                                 const double *recb, const float4 *coef, float4 *tab)
+// One CTA per (n, GT_THREADS geometries): row n of the plan's coefficients
+// is staged in shared memory, so each thread's recursion chain reads only
+// shared memory.  The FP64 pipe is narrow, so the chains are spread thinly
+// over many SMs.
+constexpr int GT_THREADS = 8;
+
+__global__ void __launch_bounds__(GT_THREADS) gim_table_kernel(const GeomRec *rec, int n_geom, int n_j, const double *A,
+                                                      const double *recb, const float4 *coef, float4 *tab)
 {
-    int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= n_geom * NP1) return;
-    int g = id / NP1, n = id % NP1;
-    double k = rec[g].k;
-    double x = 1.0 - k / (1.0 + k);
-    const double *An = A + (size_t)n * n_j;
-    const double *rb = recb + (size_t)n * n_j * 3;
-    const float4 *cf = coef + (size_t)n * n_j;
+    extern __shared__ __align__(16) unsigned char tsm[];
+    float4 *scf = reinterpret_cast<float4 *>(tsm);            // [n_j]
+    double *sA = reinterpret_cast<double *>(scf + n_j);       // [n_j]
+    double *srb = sA + n_j;                                   // [n_j][3]
+    const int n = blockIdx.y;
+    const int NP1 = gridDim.y;
+    for (int i = threadIdx.x; i < n_j; i += blockDim.x) {
+        scf[i] = coef[(size_t)n * n_j + i];
+        sA[i] = A[(size_t)n * n_j + i];
+    }
+    for (int i = threadIdx.x; i < 3 * n_j; i += blockDim.x) srb[i] = recb[(size_t)n * n_j * 3 + i];
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_geom) return;
+    const double k = rec[g].k;
+    const double x = 1.0 - k / (1.0 + k);
     float4 *out = tab + ((size_t)g * NP1 + n) * n_j;
     double gp = 0.0, gc = 1.0;
     for (int j = 0; j < n_j; ++j) {
-        float4 c = cf[j];
-        float r3n = (j + 1 < n_j) ? cf[j + 1].z : 0.0f;
-        out[j] = make_float4(c.x, c.y, r3n, (float)(An[j] * gc * gc));
-        double gn = (rb[3 * j] + rb[3 * j + 1] * x) * gc + rb[3 * j + 2] * gp;
+        float4 c = scf[j];
+        float r3n = (j + 1 < n_j) ? scf[j + 1].z : 0.0f;
+        out[j] = make_float4(c.x, c.y, r3n, (float)(sA[j] * gc * gc));
+        double gn = (srb[3 * j] + srb[3 * j + 1] * x) * gc + srb[3 * j + 2] * gp;
         gp = gc;
         gc = gn;
     }
 }
+
+size_t gim_table_smem(int n_j) { return (size_t)n_j * (sizeof(float4) + 4 * sizeof(double)); }
 
 __global__ void ssr_reduce_kernel(const float *part, int rows, int n_tiles, float *ssr)
 {
@@ -1132,10 +1213,9 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
     int *cnt = (int *)(wb + L.cnt);
     st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, cnt, s);
     if (st) return st;
-    const int tot = n_geom * NP1;
-    // FP64 recursion chains: small blocks spread them over many SMs
-    gim_table_kernel<<<(tot + 15) / 16, 16, 0, s>>>(rec, n_geom, NP1, plan->n_j, plan->d_A, plan->d_recb,
-                                                   plan->d_coef, T);
+    gim_table_kernel<<<dim3((n_geom + GT_THREADS - 1) / GT_THREADS, NP1), GT_THREADS, gim_table_smem(plan->n_j),
+                       s>>>(
+        rec, n_geom, plan->n_j, plan->d_A, plan->d_recb, plan->d_coef, T);
     st = check_launch("gim_table_kernel");
     if (st) return st;
     GimArgs A;
@@ -1157,7 +1237,7 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
     A.pref = (int *)(wb + L.pref);
     A.ctr = cnt + n_geom;
     A.list = (int *)(wb + L.list);
-    A.ppi = (n_ss >= 2) ? GS_THREADS / 2 : GS_THREADS;
+    A.ppi = (n_ss >= 20) ? GS_THREADS / 2 : GS_THREADS;
     A.n_bad = n_bad;
     gim_window_kernel<<<dim3(n_tiles, gy), TT, 0, s>>>(A);
     st = check_launch("gim_window_kernel");
@@ -1165,25 +1245,27 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
     gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, A.ppi, A.pref, A.ctr);
     st = check_launch("gim_scan_kernel");
     if (st) return st;
-    // supersamples per thread: h = n_ss split over the pair's threads,
-    // taken SB at a time (the last block of a ragged h is masked)
+    // supersamples per thread: h = n_ss, or half of it when two threads
+    // share a pair; blocks of SB = 1 without supersampling, else an even SB
+    // (two supersamples per two-lane FMA) with the least masked tail
     const int h = (A.ppi < GS_THREADS) ? (n_ss + 1) / 2 : n_ss;
     const size_t max_items = (size_t)n_geom * ((n_t + A.ppi - 1) / A.ppi);
-    if (h <= 5) {
-        switch (h) {
-        case 1: st = launch_series<1>(A, smem, max_items, s); break;
-        case 2: st = launch_series<2>(A, smem, max_items, s); break;
-        case 3: st = launch_series<3>(A, smem, max_items, s); break;
-        case 4: st = launch_series<4>(A, smem, max_items, s); break;
-        default: st = launch_series<5>(A, smem, max_items, s); break;
-        }
-    } else if (h % 5 == 0) {
-        st = launch_series<5>(A, smem, max_items, s);
-    } else if (h % 3 == 0) {
-        st = launch_series<3>(A, smem, max_items, s);
-    } else {
+    if (h == 1)
+        st = launch_series<1>(A, smem, max_items, s);
+    else if (h <= 2)
+        st = launch_series<2>(A, smem, max_items, s);
+    else if (h <= 4)
         st = launch_series<4>(A, smem, max_items, s);
-    }
+    else if (h <= 6)
+        st = launch_series<6>(A, smem, max_items, s);
+    else if (h <= 8)
+        st = launch_series<8>(A, smem, max_items, s);
+    else if (h % 10 == 0 || h % 10 > 8)
+        st = launch_series<10>(A, smem, max_items, s);
+    else if (h % 8 == 0 || h % 8 > 6)
+        st = launch_series<8>(A, smem, max_items, s);
+    else
+        st = launch_series<6>(A, smem, max_items, s);
     if (st) return st;
     if (ssr) {
         ssr_rows_kernel<<<orb->n_v * n_b, 256, 0, s>>>(A.flux, y, wt, n_t, n_b, ssr);

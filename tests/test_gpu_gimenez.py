@@ -72,6 +72,31 @@ def test_gimenez_lc_vs_oracle(torch_cuda, n_t, n_v, n_ss, n_j):
     assert np.max(np.abs(f - ref)) <= TOL
 
 
+
+@pytest.mark.parametrize("N,n_ss", [(1, 4), (3, 7), (16, 2), (8, 20), (4, 25)])
+def test_gimenez_lc_series_orders(torch_cuda, N, n_ss):
+    """Odd and even N, the largest N, supersample counts that leave masked
+    lanes in the two-lane blocks, and long supersample lists (n_ss >= 20)
+    that two threads share per pair."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=3, n_t=900, n_ss=n_ss, cadence=0.01)
+    rng = np.random.default_rng(100 + N)
+    u = np.zeros((3, 1, N))
+    u[..., 0] = rng.uniform(0.3, 0.6, (3, 1))
+    if N > 1:
+        u[..., 1] = rng.uniform(0.0, 0.2, (3, 1))
+    if N > 2:
+        u[..., 2:] = rng.uniform(-0.02, 0.02, (3, 1, N - 2))
+    wl["ld"] = wl["ld_gim"] = u
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(N, 64)
+    flux, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=n_ss, t_exp=wl["t_exp"])
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = _oracle_lc(wl, 64)
+    assert (ref < 1).sum() > 0
+    assert np.max(np.abs(f - ref)) <= TOL
+
 def test_gimenez_ssr_and_multiband(torch_cuda):
     import paper_1504_07433_gb300 as pt
     torch = torch_cuda
