@@ -631,48 +631,83 @@ __global__ void __launch_bounds__(GS_THREADS, GS_MIN_CTAS) gim_series_kernel(Gim
 
 size_t gim_series_smem(int N, int n_j) { return (size_t)(N + 1) * n_j * sizeof(float4); }
 
+// Double-float arithmetic for the table recursion: a value is the unevaluated
+// sum h + l of two floats (about 48 significant bits).  Sums and products
+// carry their rounding errors exactly (Knuth's two-sum; the FMA form of
+// Dekker's product).  GB300's FP64 rate is a small fraction of its FP32
+// rate, so a chain of FP64 operations would dominate this kernel.
+struct DF {
+    float h, l;
+};
+
+__device__ __forceinline__ DF df_of(double v)
+{
+    float h = (float)v;
+    return DF{h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ DF df_norm(float s, float e)   // |s| >= |e|
+{
+    float h = s + e;
+    return DF{h, e - (h - s)};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    float s = a.h + b.h;
+    float bb = s - a.h;
+    float e = (a.h - (s - bb)) + (b.h - bb);
+    return df_norm(s, e + (a.l + b.l));
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    return df_norm(p, e);
+}
+
 // Gimenez per-geometry table for Clenshaw's summation: entry (n, j) packs the
 // z-recursion coefficients r1_j, r2_j, r3_{j+1} of G_j(nu+2, 1; x) with
 // T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2, the z-independent factor of
-// Sec. 2.1.4 (FP64 recursion, stored FP32).
-// One CTA per (n, GT_THREADS geometries): row n of the plan's coefficients
-// is staged in shared memory, so each thread's recursion chain reads only
-// shared memory.  The FP64 pipe is narrow, so the chains are spread thinly
-// over many SMs.
-constexpr int GT_THREADS = 8;
-
-__global__ void __launch_bounds__(GT_THREADS) gim_table_kernel(const GeomRec *rec, int n_geom, int n_j, const double *A,
+// Sec. 2.1.4 (recursion in double-float arithmetic, stored FP32).
+// One CTA per (n, 32 geometries): row n of the plan's coefficients is staged
+// in shared memory as double-float pairs.
+__global__ void __launch_bounds__(32) gim_table_kernel(const GeomRec *rec, int n_geom, int n_j, const double *A,
                                                       const double *recb, const float4 *coef, float4 *tab)
 {
     extern __shared__ __align__(16) unsigned char tsm[];
-    float4 *scf = reinterpret_cast<float4 *>(tsm);            // [n_j]
-    double *sA = reinterpret_cast<double *>(scf + n_j);       // [n_j]
-    double *srb = sA + n_j;                                   // [n_j][3]
+    float4 *scf = reinterpret_cast<float4 *>(tsm);   // [n_j]
+    DF *sA = reinterpret_cast<DF *>(scf + n_j);      // [n_j]
+    DF *srb = sA + n_j;                              // [n_j][3]
     const int n = blockIdx.y;
     const int NP1 = gridDim.y;
     for (int i = threadIdx.x; i < n_j; i += blockDim.x) {
         scf[i] = coef[(size_t)n * n_j + i];
-        sA[i] = A[(size_t)n * n_j + i];
+        sA[i] = df_of(A[(size_t)n * n_j + i]);
     }
-    for (int i = threadIdx.x; i < 3 * n_j; i += blockDim.x) srb[i] = recb[(size_t)n * n_j * 3 + i];
+    for (int i = threadIdx.x; i < 3 * n_j; i += blockDim.x) srb[i] = df_of(recb[(size_t)n * n_j * 3 + i]);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_geom) return;
     const double k = rec[g].k;
-    const double x = 1.0 - k / (1.0 + k);
+    const DF x = df_of(1.0 - k / (1.0 + k));
     float4 *out = tab + ((size_t)g * NP1 + n) * n_j;
-    double gp = 0.0, gc = 1.0;
+    DF gp = DF{0.0f, 0.0f}, gc = DF{1.0f, 0.0f};
     for (int j = 0; j < n_j; ++j) {
         float4 c = scf[j];
         float r3n = (j + 1 < n_j) ? scf[j + 1].z : 0.0f;
-        out[j] = make_float4(c.x, c.y, r3n, (float)(sA[j] * gc * gc));
-        double gn = (srb[3 * j] + srb[3 * j + 1] * x) * gc + srb[3 * j + 2] * gp;
+        DF t = df_mul(df_mul(sA[j], gc), gc);
+        out[j] = make_float4(c.x, c.y, r3n, t.h + t.l);
+        DF al = df_add(srb[3 * j], df_mul(srb[3 * j + 1], x));
+        DF gn = df_add(df_mul(al, gc), df_mul(srb[3 * j + 2], gp));
         gp = gc;
         gc = gn;
     }
 }
 
-size_t gim_table_smem(int n_j) { return (size_t)n_j * (sizeof(float4) + 4 * sizeof(double)); }
+size_t gim_table_smem(int n_j) { return (size_t)n_j * (sizeof(float4) + 4 * sizeof(DF)); }
 
 __global__ void ssr_reduce_kernel(const float *part, int rows, int n_tiles, float *ssr)
 {
@@ -1213,8 +1248,7 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
     int *cnt = (int *)(wb + L.cnt);
     st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, cnt, s);
     if (st) return st;
-    gim_table_kernel<<<dim3((n_geom + GT_THREADS - 1) / GT_THREADS, NP1), GT_THREADS, gim_table_smem(plan->n_j),
-                       s>>>(
+    gim_table_kernel<<<dim3((n_geom + 31) / 32, NP1), 32, gim_table_smem(plan->n_j), s>>>(
         rec, n_geom, plan->n_j, plan->d_A, plan->d_recb, plan->d_coef, T);
     st = check_launch("gim_table_kernel");
     if (st) return st;
