@@ -82,6 +82,11 @@ def _lib():
                 ("pto_flux_theta", _D, [_D, _PD, _I, _D]),
                 ("pto_flux_grad", _D, [_D, _PD, _I, _D, _PD]),
                 ("pto_ssr_grad", None, [_PD, _I, _PD, _I, _I, _D, _PD, _PD, _PD, _PD, _I]),
+                ("pto_ma_table", None, [_D, _D, _I, _I, _PD]),
+                ("pto_ma_interp", None, [_PD, _D, _D, _I, _I, _D, _D, _PD]),
+                ("pto_flux_quad_interp", _D, [_PD, _D, _D, _I, _I, _D, _D, _D, _D]),
+                ("pto_lc_ma_interp", _I, [_PD, _D, _D, _I, _I, _PD, _I, _PD, _PD, _PD, _PD, _PD, _PD, _I,
+                                          _PD, _I, _PD, _I, _I, _D, _PD, _I]),
                 ("pto_mlp_nparams", _I, []),
                 ("pto_mlp_forward", None, [_PD, _PD, _I, _PD]),
                 ("pto_mlp_loss_grad", _D, [_PD, _PD, _PD, _I, _PD]),
@@ -237,6 +242,54 @@ def lc_ma(t, orbit, k, ld, n_ss=1, t_exp=0.0, n_threads=0):
     flux = np.zeros((n_v, n_b, t.size))
     nbad = _lib().pto_lc_ma(_ptr(t), t.size, _ptr(t0), _ptr(P), _ptr(a), _ptr(inc), _ptr(e), _ptr(w), n_v,
                             _ptr(k), kpb, _ptr(ld), n_b, n_ss, t_exp, _ptr(flux), n_threads)
+    return flux, nbad
+
+
+class MATable:
+    """Interpolation table of the Mandel-Agol terms (Sec. 2.2.3): n_k radius
+    ratios over [k_lo, k_hi] x n_z separations over [0, 1 + k_hi]; the values
+    are (lambda_e, lambda_d + 2/3 Theta(k - z), eta_d) of ma_terms."""
+
+    def __init__(self, k_lo, k_hi, n_k, n_z):
+        if n_k < 2 or n_z < 2 or not k_hi > k_lo:
+            raise ValueError("need n_k, n_z >= 2 and k_hi > k_lo")
+        self.k_lo, self.k_hi, self.n_k, self.n_z = float(k_lo), float(k_hi), int(n_k), int(n_z)
+        self.tab = np.zeros((n_k, n_z, 3))
+        _lib().pto_ma_table(self.k_lo, self.k_hi, self.n_k, self.n_z, _ptr(self.tab))
+
+    def _args(self):
+        return _ptr(self.tab), self.k_lo, self.k_hi, self.n_k, self.n_z
+
+    def terms(self, k, z):
+        """Interpolated (lambda_e, lambda_d + 2/3 Theta, eta_d) for one (k, z)."""
+        out = np.zeros(3)
+        _lib().pto_ma_interp(*self._args(), float(k), float(z), _ptr(out))
+        return out
+
+    def terms_vec(self, k, z):
+        k = np.broadcast_to(np.asarray(k, dtype=np.float64), np.shape(z)).ravel()
+        z = np.asarray(z, dtype=np.float64).ravel()
+        out = np.zeros((z.size, 3))
+        for i in range(z.size):
+            out[i] = self.terms(k[i], z[i])
+        return out
+
+    def flux(self, k, z, u1, u2):
+        return _lib().pto_flux_quad_interp(*self._args(), float(k), float(z), float(u1), float(u2))
+
+
+def lc_ma_interp(table, t, orbit, k, ld, n_ss=1, t_exp=0.0, n_threads=0):
+    """lc_ma with the terms read from an MATable (Sec. 2.2.3)."""
+    t = _arr(t)
+    ld = np.ascontiguousarray(np.asarray(ld, dtype=np.float64))
+    n_v, n_b = ld.shape[0], ld.shape[1]
+    t0, P, a, inc, e, w = _orbit(orbit, n_v)
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.float64))
+    kpb = 1 if k.ndim == 2 else 0
+    flux = np.zeros((n_v, n_b, t.size))
+    nbad = _lib().pto_lc_ma_interp(*table._args(), _ptr(t), t.size, _ptr(t0), _ptr(P), _ptr(a), _ptr(inc),
+                                   _ptr(e), _ptr(w), n_v, _ptr(k), kpb, _ptr(ld), n_b, n_ss, t_exp, _ptr(flux),
+                                   n_threads)
     return flux, nbad
 
 

@@ -18,6 +18,7 @@
  *     Eq. (ld_general), Sec. 2.1.3 (C_n), Sec. 2.1.4 (A_{n,j} and the Jacobi
  *     recursion): the Gimenez series model.
  *   - Sec. 3.2: exposure supersampling.
+ *   - Sec. 2.2.3: interpolation tables of the Mandel-Agol terms.
  *   - Sec. 1: circular orbits and eccentric orbits solved with Newton's
  *     method (the paper names the solver but prints no formula).
  *   - Carlson (1995, Numer. Algorithms 10, 13): symmetric elliptic integrals
@@ -273,6 +274,66 @@ double pto_flux_quad(double p, double z, double u1, double u2)
 }
 
 /* ------------------------------------------------------------------------
+ * Interpolated Mandel-Agol terms (Sec. 2.2.3).  lambda_e, lambda_d + 2/3
+ * Theta(p - z) (continuous in z, unlike lambda_d alone) and eta_d are
+ * tabulated on the grid
+ *   k_i = k_lo + i (k_hi - k_lo) / (n_k - 1),   i = 0 .. n_k - 1,
+ *   z_j = j (1 + k_hi) / (n_z - 1),             j = 0 .. n_z - 1,
+ * i.e. z spans [0, 1 + k] for every k of the table, and read back by
+ * bilinear interpolation (linear in k, then in z).  Readings: out of transit
+ * (z >= 1 + k) the terms are zero, as for the exact model; k outside
+ * [k_lo, k_hi] is clamped to the table's range.
+ * ---------------------------------------------------------------------- */
+void pto_ma_table(double k_lo, double k_hi, int n_k, int n_z, double *tab /* [n_k][n_z][3] */)
+{
+    for (int i = 0; i < n_k; ++i) {
+        double k = k_lo + i * (k_hi - k_lo) / (n_k - 1);
+        for (int j = 0; j < n_z; ++j) {
+            double z = j * (1.0 + k_hi) / (n_z - 1);
+            double t[3];
+            pto_ma_terms(k, z, t);
+            if (k > z) t[1] += 2.0 / 3.0;
+            for (int c = 0; c < 3; ++c) tab[((size_t)i * n_z + j) * 3 + c] = t[c];
+        }
+    }
+}
+
+void pto_ma_interp(const double *tab, double k_lo, double k_hi, int n_k, int n_z, double k, double z,
+                   double *out /* [3] */)
+{
+    out[0] = out[1] = out[2] = 0.0;
+    if (!(z < 1.0 + k)) return;
+    double fk = (k - k_lo) / ((k_hi - k_lo) / (n_k - 1));
+    if (fk < 0.0) fk = 0.0;
+    if (fk > n_k - 1) fk = n_k - 1;
+    int ik = (int)floor(fk);
+    if (ik > n_k - 2) ik = n_k - 2;
+    double wk = fk - ik;
+    double fz = z / ((1.0 + k_hi) / (n_z - 1));
+    if (fz < 0.0) fz = 0.0;
+    if (fz > n_z - 1) fz = n_z - 1;
+    int iz = (int)floor(fz);
+    if (iz > n_z - 2) iz = n_z - 2;
+    double wz = fz - iz;
+    for (int c = 0; c < 3; ++c) {
+        double a = tab[((size_t)ik * n_z + iz) * 3 + c], b = tab[((size_t)ik * n_z + iz + 1) * 3 + c];
+        double d = tab[((size_t)(ik + 1) * n_z + iz) * 3 + c], e = tab[((size_t)(ik + 1) * n_z + iz + 1) * 3 + c];
+        out[c] = (1.0 - wk) * ((1.0 - wz) * a + wz * b) + wk * ((1.0 - wz) * d + wz * e);
+    }
+}
+
+/* Eq. (ma_model) from interpolated terms (the Theta term is in out[1]). */
+double pto_flux_quad_interp(const double *tab, double k_lo, double k_hi, int n_k, int n_z, double p, double z,
+                            double u1, double u2)
+{
+    double t[3];
+    pto_ma_interp(tab, k_lo, k_hi, n_k, n_z, p, z, t);
+    if (t[0] == 0.0 && t[1] == 0.0 && t[2] == 0.0) return 1.0;
+    double c = u1 + 2.0 * u2;
+    return 1.0 - ((1.0 - c) * t[0] + c * t[1] + u2 * t[2]) / (1.0 - u1 / 3.0 - u2 / 6.0);
+}
+
+/* ------------------------------------------------------------------------
  * Gimenez (2006) series, Sec. 2.1.
  * ---------------------------------------------------------------------- */
 
@@ -468,6 +529,38 @@ int pto_lc_ma(const double *t, int n_t, const double *t0, const double *P, const
                     double kk = k_per_band ? k[(size_t)v * n_b + b] : k[v];
                     const double *u = ld + ((size_t)v * n_b + b) * 2;
                     flux[((size_t)v * n_b + b) * n_t + i] += pto_flux_quad(kk, z, u[0], u[1]);
+                }
+            }
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] /= n_ss;
+        }
+    }
+    return nbad;
+}
+
+/* pto_lc_ma with the terms read from an interpolation table (Sec. 2.2.3). */
+int pto_lc_ma_interp(const double *tab, double k_lo, double k_hi, int n_k, int n_z, const double *t, int n_t,
+                     const double *t0, const double *P, const double *a, const double *inc, const double *e,
+                     const double *w, int n_v, const double *k, int k_per_band, const double *ld /* [v][b][2] */,
+                     int n_b, int n_ss, double t_exp, double *flux /* [v][b][t] */, int n_threads)
+{
+    int nbad = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#endif
+    for (int v = 0; v < n_v; ++v) {
+        for (int i = 0; i < n_t; ++i) {
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] = 0.0;
+            for (int s = 0; s < n_ss; ++s) {
+                double tt = t[i] + t_exp * ((s + 0.5) / n_ss - 0.5);
+                int bad = 0;
+                double z = orbit_z(t0, P, a, inc, e, w, v, tt, &bad);
+                nbad += bad;
+                for (int b = 0; b < n_b; ++b) {
+                    double kk = k_per_band ? k[(size_t)v * n_b + b] : k[v];
+                    const double *u = ld + ((size_t)v * n_b + b) * 2;
+                    flux[((size_t)v * n_b + b) * n_t + i] +=
+                        pto_flux_quad_interp(tab, k_lo, k_hi, n_k, n_z, kk, z, u[0], u[1]);
                 }
             }
             for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] /= n_ss;
