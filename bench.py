@@ -245,8 +245,31 @@ def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000, epochs=40):
     def run_sur():
         model.terms(k, z, nfb, work, outs)
 
+    # the paper's interpolation tables (Sec. 2.2.3) over the same k range, with
+    # a grid fine enough that their error is comparable with the surrogate's
+    # (over this wide k range the k spacing dominates the error in the band:
+    # the contact z = 1 + k moves across a cell)
+    import paper_1504_07433_gb300 as pt
+    itab = pt.MATable(0.01, 0.3, 512, 2048)
+
+    def run_interp():
+        from paper_1504_07433_gb300 import _check, _ptr, _stream
+        _check(S.lib().pt_ma_terms_interp(itab.handle, _ptr(k), _ptr(z), z.numel(), _ptr(outs[0]), _ptr(outs[1]),
+                                          _ptr(outs[2]), _stream()), "pt_ma_terms_interp")
+
+    # flux-error bound of the table on the first 1e7 points (q1, q2 in [0, 1]:
+    # 2 |d lambda_e| + 4 |d lambda_d| + 2 |d eta_d|)
+    n_chk = min(10_000_000, z.numel())
+    run_exact()
+    ref = tuple(o[:n_chk].clone() for o in outs)
+    run_interp()
+    interp_bound = float((2 * (outs[0][:n_chk] - ref[0]).abs() + 4 * (outs[1][:n_chk] - ref[1]).abs()
+                          + 2 * (outs[2][:n_chk] - ref[2]).abs()).max().item())
+    del ref
+
     res = {}
-    for name, fn in (("exact", run_exact), ("surrogate", run_sur)):
+    share = None
+    for name, fn in (("exact", run_exact), ("surrogate", run_sur), ("interp", run_interp)):
         fn()
         torch.cuda.synchronize()
         ms = []
@@ -260,7 +283,8 @@ def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000, epochs=40):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         res[name] = float(np.mean(ms))
-    share = 1.0 - int(nfb.item()) / n_infer
+        if name == "surrogate":
+            share = 1.0 - int(nfb.item()) / n_infer
     out = {"workload": "%.0e (k, z) points over k in [0.01, 0.3], z in [|1-k|, 1+k]" % n_infer,
            "train_s": t_train, "train_samples": 10_000_000, "epochs": epochs,
            "table_cells_exact": float(table.mean()), "network_share": share,
@@ -268,11 +292,49 @@ def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000, epochs=40):
            "exact_points_per_s": n_infer / (res["exact"] * 1e-3),
            "surrogate_points_per_s": n_infer / (res["surrogate"] * 1e-3),
            "gain_vs_exact": res["exact"] / res["surrogate"], "timed_out": model.timed_out(),
+           "interp_table": "k in [0.01, 0.3], n_k = 512, n_z = 2048 (Sec. 2.2.3)", "interp_ms": res["interp"],
+           "interp_points_per_s": n_infer / (res["interp"] * 1e-3), "interp_gain_vs_exact": res["exact"] / res["interp"],
+           "interp_flux_err_bound_1e7": interp_bound,
            "tensor_tflops": share * n_infer * 2 * 2 * 128 * 128 / (res["surrogate"] * 1e-3) / 1e12}
     model.close()
+    itab.close()
     del k, z, outs, work
     torch.cuda.empty_cache()
     return out
+
+
+def bench_ma_interp(pt, torch, dev, stream, K, flush, t, orb, k, ld, wl, f_exact, k_lo=0.05, k_hi=0.2):
+    """Interpolated Mandel-Agol light curves (Sec. 2.2.3) on the long-cadence
+    workload: a table over the workload's k range at the paper's default grid
+    (n_k = 128, n_z = 256), timed like the exact MA call, and its largest flux
+    difference from the exact FP32 path."""
+    tab = pt.MATable(k_lo, k_hi, 128, 256)
+    n_t, n_v = t.numel(), k.numel()
+    work = torch.empty(pt.ma_quad_work_bytes(n_t, n_v, 1), dtype=torch.uint8, device=dev)
+    f = torch.empty_like(f_exact)
+
+    def run():
+        pt.ma_quad_interp(tab, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=work, flux=f)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(K):
+        flush.fill_(i & 0xff)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    m = float(np.mean(ms))
+    err = float((f.double() - f_exact.double()).abs().max().item())
+    tab.close()
+    return {"workload": wl["name"], "table": "k in [%.2f, %.2f], n_k = 128, n_z = 256" % (k_lo, k_hi),
+            "ms_per_call": m, "value": n_t * n_v / (m * 1e-3), "unit": "flux points/s",
+            "max_abs_diff_vs_exact": err, "gpu_launches_per_call": 2}
 
 
 def only_main(args):
@@ -492,8 +554,9 @@ def main():
                 "peak_source": "FP32 lanes 152 SM x 128 x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_max, peak_src),
                 "algorithmic_flops_per_launch": flops, "in_transit_evaluations": n_intr}
 
-    adjoint = batched = surrogate = None
+    adjoint = batched = surrogate = ma_interp = None
     if not args.no_extra:
+        ma_interp = bench_ma_interp(pt, torch, dev, stream, K, flush, t, orb, k, ld, wl, fm)
         adjoint = bench_adjoint(pt, torch, dev, stream, K, flush)
         batched = bench_batched(pt, torch, dev, stream, K, flush)
         surrogate = bench_surrogate(torch, dev, stream)
@@ -522,7 +585,7 @@ def main():
                            "parallelism": "replicas x%d" % ws},
                 "components_ms": {"ma_quad": float(np.mean(ma_ms)), "gimenez": g_mean_ms},
                 "max_abs_err_vs_oracle": max_err,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "adjoint": adjoint,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ma_interp": ma_interp, "adjoint": adjoint,
                 "batched": batched, "surrogate": surrogate,
                 "gpu_launches": 7 * K, "clocks": dict(clocks, window="%.1f s of untimed steps + the timed region"
                                                       % args.heat_s) if clocks else None,

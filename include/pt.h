@@ -154,6 +154,39 @@ int pt_ma_quad(const double *t_dev, int n_t, const pt_orbit *orb, const float *k
                int *n_bad_dev, pt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Interpolated Mandel-Agol terms (Sec. 2.2.3).  The three functions of
+ * Eq. (ma_model) are tabulated on a (k, z) grid and read back by bilinear
+ * interpolation instead of being evaluated:
+ *   k_i = k_lo + i (k_hi - k_lo) / (n_k - 1),   i = 0 .. n_k - 1,
+ *   z_j = j (1 + k_hi) / (n_z - 1),             j = 0 .. n_z - 1
+ * (z spans [0, 1 + k] for every k of the table), values
+ * (lambda_e, lambda_d + 2/3 Theta(k - z), eta_d) as in pt_ma_terms, computed
+ * by the exact FP32 kernel.  Reading: z >= 1 + k gives exactly zero (out of
+ * transit); k outside [k_lo, k_hi] is clamped to the table's range (the
+ * caller sets the range from the prior on k).  The paper's defaults are
+ * n_k = 128, n_z = 256; the error against the exact model is dominated by
+ * n_z (a few ppm in flux at n_z = 256).
+ *
+ *   pt_ma_table_create   builds the table on the device (allocates
+ *                        n_k n_z 16 bytes; requires 0 < k_lo < k_hi,
+ *                        2 <= n_k <= 4096, 2 <= n_z <= 65536); synchronous.
+ *   pt_ma_table_destroy  frees it.
+ *   pt_ma_terms_interp   pointwise drop-in for pt_ma_terms.
+ *   pt_ma_quad_interp    pt_ma_quad with the interpolated terms (same
+ *                        arguments, same work buffer size).
+ * ---------------------------------------------------------------------- */
+typedef struct pt_ma_table_s *pt_ma_table;
+
+int pt_ma_table_create(float k_lo, float k_hi, int n_k, int n_z, pt_ma_table *table_out);
+int pt_ma_table_destroy(pt_ma_table table);
+int pt_ma_terms_interp(pt_ma_table table, const float *k_dev, const float *z_dev, size_t n, float *lam_e_dev,
+                       float *lam_d_dev, float *eta_d_dev, pt_stream_t stream);
+int pt_ma_quad_interp(pt_ma_table table, const double *t_dev, int n_t, const pt_orbit *orb, const float *k_dev,
+                      int k_per_band, const float *ld_dev, int n_b, int n_ss, double t_exp, int max_iter,
+                      const float *y_dev, const float *wt_dev, float *flux_dev, float *ssr_dev, void *work_dev,
+                      size_t work_bytes, int *n_bad_dev, pt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint of the quadratic Mandel-Agol light curve (not in the paper, which
  * cites analytic MA derivatives, Pal 2008).  For n_v parameter vectors
  * theta = (t0, P, a, b, e, w, k, u1, u2), one passband, exposure times t:

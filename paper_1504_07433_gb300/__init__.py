@@ -19,6 +19,7 @@ import os
 from . import build as _build_mod
 
 __all__ = ["load_library", "Orbit", "Theta", "orbit_to_device", "z_circ", "z_ecc", "ma_terms", "ma_quad",
+           "MATable", "ma_terms_interp", "ma_quad_interp",
            "ma_quad_work_bytes", "GimenezPlan", "gimenez", "gimenez_alpha", "ma_quad_bwd", "transit_ssr",
            "PTError", "Z_BEHIND"]
 
@@ -75,6 +76,11 @@ def load_library(build_if_missing: bool = False):
         "pt_ma_quad_work_bytes": (_c_size, [_c_int, _c_int, _c_int, _c_int]),
         "pt_ma_quad": (_c_int, [P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int, _c_double, _c_int,
                                 P, P, P, P, P, _c_size, P, P]),
+        "pt_ma_table_create": (_c_int, [ctypes.c_float, ctypes.c_float, _c_int, _c_int, ctypes.POINTER(_c_void_p)]),
+        "pt_ma_table_destroy": (_c_int, [P]),
+        "pt_ma_terms_interp": (_c_int, [P, P, P, _c_size, P, P, P, P]),
+        "pt_ma_quad_interp": (_c_int, [P, P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int,
+                                       _c_double, _c_int, P, P, P, P, P, _c_size, P, P]),
         "pt_gim_plan_create": (_c_int, [_c_int, _c_int, ctypes.POINTER(_c_void_p)]),
         "pt_gim_plan_destroy": (_c_int, [P]),
         "pt_gimenez_alpha": (_c_int, [P, P, P, _c_size, P, P]),
@@ -219,6 +225,65 @@ def ma_quad(t, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None, want
     _check(lib.pt_ma_quad(_ptr(t), n_t, ctypes.byref(o), _ptr(k), kpb, _ptr(ld), n_b, int(n_ss), float(t_exp),
                           int(max_iter), _ptr(y), _ptr(wt), _ptr(fl), _ptr(ss), _ptr(work), work.numel(),
                           _ptr(n_bad), _stream()), "pt_ma_quad")
+    return fl, ss
+
+
+class MATable:
+    """Interpolation table of the Mandel-Agol terms (Sec. 2.2.3;
+    pt_ma_table_create): n_k radius ratios over [k_lo, k_hi] x n_z separations
+    over [0, 1 + k_hi], read by bilinear interpolation."""
+
+    def __init__(self, k_lo, k_hi, n_k=128, n_z=256):
+        lib = load_library()
+        h = _c_void_p()
+        _check(lib.pt_ma_table_create(float(k_lo), float(k_hi), int(n_k), int(n_z), ctypes.byref(h)),
+               "pt_ma_table_create")
+        self.handle = h
+        self.k_lo, self.k_hi, self.n_k, self.n_z = float(k_lo), float(k_hi), int(n_k), int(n_z)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load_library().pt_ma_table_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ma_terms_interp(table, k, z):
+    """Interpolated (lambda_e, lambda_d + 2/3 Theta(k-z), eta_d) for (k, z)
+    pairs (pt_ma_terms_interp)."""
+    torch = _torch()
+    lib = load_library()
+    k = k.contiguous()
+    z = z.contiguous()
+    le = torch.empty_like(z)
+    ld = torch.empty_like(z)
+    ed = torch.empty_like(z)
+    _check(lib.pt_ma_terms_interp(table.handle, _ptr(k), _ptr(z), z.numel(), _ptr(le), _ptr(ld), _ptr(ed),
+                                  _stream()), "pt_ma_terms_interp")
+    return le, ld, ed
+
+
+def ma_quad_interp(table, t, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None, want_flux=True,
+                   want_ssr=False, work=None, flux=None, ssr=None, n_bad=None):
+    """ma_quad with the terms read from an MATable (pt_ma_quad_interp)."""
+    torch = _torch()
+    lib = load_library()
+    o, n_v = _orbit_struct(orb)
+    n_b = int(ld.shape[1])
+    kpb = 1 if k.dim() == 2 else 0
+    n_t = t.numel()
+    fl, ss = _lc_outputs(n_v, n_b, n_t, want_flux, want_ssr, t.device, flux, ssr)
+    need = int(lib.pt_ma_quad_work_bytes(n_t, n_v, n_b, kpb))
+    if work is None or work.numel() < need:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=t.device)
+    _check(lib.pt_ma_quad_interp(table.handle, _ptr(t), n_t, ctypes.byref(o), _ptr(k), kpb, _ptr(ld), n_b,
+                                 int(n_ss), float(t_exp), int(max_iter), _ptr(y), _ptr(wt), _ptr(fl), _ptr(ss),
+                                 _ptr(work), work.numel(), _ptr(n_bad), _stream()), "pt_ma_quad_interp")
     return fl, ss
 
 

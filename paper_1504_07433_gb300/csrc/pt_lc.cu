@@ -127,7 +127,40 @@ struct LcArgs {
     float *ssr_part;     // [rows][n_tiles]
     int n_tiles;
     int *n_bad;
+    // interpolated Mandel-Agol terms (Sec. 2.2.3), when the kernel uses them
+    const float4 *mtab;  // [n_k][n_z]: (lambda_e, lambda_d + 2/3 Theta, eta_d, 0)
+    int mn_k, mn_z;
+    float mk_lo, mk_hi, minv_dk, minv_dz;
 };
+
+// Bilinear interpolation of the tabulated Mandel-Agol terms (Sec. 2.2.3):
+// node (i, j) holds the terms at k_i = k_lo + i dk, z_j = j dz with
+// dz = (1 + k_hi) / (n_z - 1).  Out of transit (z >= 1 + k, also the
+// behind-the-star sentinel and NaN) the terms are zero; k is clamped to the
+// table's range.
+__device__ __forceinline__ void ma_interp(const float4 *tab, int n_k, int n_z, float k_lo, float k_hi,
+                                          float inv_dk, float inv_dz, float k, float z, float *le, float *ld,
+                                          float *ed)
+{
+    *le = 0.0f;
+    *ld = 0.0f;
+    *ed = 0.0f;
+    if (!(z < 1.0f + k)) return;
+    float fk = (fminf(fmaxf(k, k_lo), k_hi) - k_lo) * inv_dk;
+    int ik = min((int)fk, n_k - 2);
+    float wk = fk - (float)ik;
+    float fz = fminf(fmaxf(z, 0.0f) * inv_dz, (float)(n_z - 1));
+    int iz = min((int)fz, n_z - 2);
+    float wz = fz - (float)iz;
+    const float4 *r0 = tab + (size_t)ik * n_z + iz;
+    const float4 *r1 = r0 + n_z;
+    float4 a = __ldg(r0), b = __ldg(r0 + 1), c = __ldg(r1), d = __ldg(r1 + 1);
+    float a0 = fmaf(wz, b.x - a.x, a.x), a1 = fmaf(wz, b.y - a.y, a.y), a2 = fmaf(wz, b.z - a.z, a.z);
+    float c0 = fmaf(wz, d.x - c.x, c.x), c1 = fmaf(wz, d.y - c.y, c.y), c2 = fmaf(wz, d.z - c.z, c.z);
+    *le = fmaf(wk, c0 - a0, a0);
+    *ld = fmaf(wk, c1 - a1, a1);
+    *ed = fmaf(wk, c2 - a2, a2);
+}
 
 __device__ __forceinline__ float block_sum(float v, float *sred)
 {
@@ -188,6 +221,7 @@ __device__ __forceinline__ float ss_offset(float t_exp, int s, int n_ss)
 // ---------------------------------------------------------------------------
 // Mandel-Agol light curves
 // ---------------------------------------------------------------------------
+template <bool INTERP>
 __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 {
     __shared__ GeomRec srec[VT_MA];
@@ -222,7 +256,10 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
             bool bad = false;
             float z = pt::orbit_z(r, dts, A.max_iter, &bad);
             if (bad) atomicAdd(&sbad, 1);
-            pt::ma_terms(r.k, z, &le, &ld, &ed);
+            if constexpr (INTERP)
+                ma_interp(A.mtab, A.mn_k, A.mn_z, A.mk_lo, A.mk_hi, A.minv_dk, A.minv_dz, r.k, z, &le, &ld, &ed);
+            else
+                pt::ma_terms(r.k, z, &le, &ld, &ed);
         }
         sub[0][tl] = le;
         sub[1][tl] = ld;
@@ -741,6 +778,33 @@ __global__ void __launch_bounds__(256) ssr_rows_kernel(const float *flux, const 
     if (threadIdx.x == 0) ssr[row] = tot;
 }
 
+// Interpolation-table nodes: the exact FP32 terms at (k_i, z_j), positions
+// formed in FP64 and rounded once.
+__global__ void ma_table_kernel(double k_lo, double k_hi, int n_k, int n_z, float4 *tab)
+{
+    size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (size_t)n_k * n_z) return;
+    int i = (int)(id / n_z), j = (int)(id % n_z);
+    float k = (float)(k_lo + i * (k_hi - k_lo) / (n_k - 1));
+    float z = (float)(j * (1.0 + k_hi) / (n_z - 1));
+    float le, ld, ed;
+    pt::ma_terms(k, z, &le, &ld, &ed);
+    tab[id] = make_float4(le, ld, ed, 0.0f);
+}
+
+__global__ void ma_terms_interp_kernel(const float4 *tab, int n_k, int n_z, float k_lo, float k_hi, float inv_dk,
+                                       float inv_dz, const float *k, const float *z, size_t n, float *le, float *ld,
+                                       float *ed)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float a, b, c;
+    ma_interp(tab, n_k, n_z, k_lo, k_hi, inv_dk, inv_dz, k[i], z[i], &a, &b, &c);
+    if (le) le[i] = a;
+    if (ld) ld[i] = b;
+    if (ed) ed[i] = c;
+}
+
 // ---------------------------------------------------------------------------
 // Pointwise kernels
 // ---------------------------------------------------------------------------
@@ -915,6 +979,12 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
 }
 
 }  // namespace
+
+struct pt_ma_table_s {
+    float k_lo, k_hi, inv_dk, inv_dz;
+    int n_k, n_z;
+    float4 *d_tab;   // [n_k][n_z]: (lambda_e, lambda_d + 2/3 Theta, eta_d, 0)
+};
 
 struct pt_gim_plan_s {
     int N, n_j;
@@ -1094,9 +1164,14 @@ static int launch_setup(const double *t, int n_t, const pt_orbit *orb, const flo
     return check_launch("setup_kernel");
 }
 
-int pt_ma_quad(const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band, const float *ld,
-               int n_b, int n_ss, double t_exp, int max_iter, const float *y, const float *wt, float *flux,
-               float *ssr, void *work, size_t work_bytes, int *n_bad, pt_stream_t stream)
+}  // extern "C"
+
+// pt_ma_quad and pt_ma_quad_interp: exact terms when tab is null, else the
+// interpolated ones.
+static int ma_quad_impl(const pt_ma_table_s *tab, const double *t, int n_t, const pt_orbit *orb, const float *k,
+                        int k_per_band, const float *ld, int n_b, int n_ss, double t_exp, int max_iter,
+                        const float *y, const float *wt, float *flux, float *ssr, void *work, size_t work_bytes,
+                        int *n_bad, pt_stream_t stream)
 {
     int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, max_iter, y, flux, ssr, work);
     if (st) return st;
@@ -1133,7 +1208,18 @@ int pt_ma_quad(const double *t, int n_t, const pt_orbit *orb, const float *k, in
     int gy = (A.n_geom + VT_MA - 1) / VT_MA;
     if (gy > 65535) return PT_ERR_ARG;
     dim3 grid(A.n_tiles, gy);
-    ma_lc_kernel<<<grid, TT, 0, s>>>(A);
+    if (tab) {
+        A.mtab = tab->d_tab;
+        A.mn_k = tab->n_k;
+        A.mn_z = tab->n_z;
+        A.mk_lo = tab->k_lo;
+        A.mk_hi = tab->k_hi;
+        A.minv_dk = tab->inv_dk;
+        A.minv_dz = tab->inv_dz;
+        ma_lc_kernel<true><<<grid, TT, 0, s>>>(A);
+    } else {
+        ma_lc_kernel<false><<<grid, TT, 0, s>>>(A);
+    }
     st = check_launch("ma_lc_kernel");
     if (st) return st;
     if (ssr) {
@@ -1142,6 +1228,76 @@ int pt_ma_quad(const double *t, int n_t, const pt_orbit *orb, const float *k, in
         st = check_launch("ssr_reduce_kernel");
     }
     return st;
+}
+
+extern "C" {
+
+int pt_ma_quad(const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band, const float *ld,
+               int n_b, int n_ss, double t_exp, int max_iter, const float *y, const float *wt, float *flux,
+               float *ssr, void *work, size_t work_bytes, int *n_bad, pt_stream_t stream)
+{
+    return ma_quad_impl(nullptr, t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux, ssr,
+                        work, work_bytes, n_bad, stream);
+}
+
+int pt_ma_quad_interp(pt_ma_table table, const double *t, int n_t, const pt_orbit *orb, const float *k,
+                      int k_per_band, const float *ld, int n_b, int n_ss, double t_exp, int max_iter, const float *y,
+                      const float *wt, float *flux, float *ssr, void *work, size_t work_bytes, int *n_bad,
+                      pt_stream_t stream)
+{
+    if (!table) return PT_ERR_ARG;
+    return ma_quad_impl(table, t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux, ssr, work,
+                        work_bytes, n_bad, stream);
+}
+
+int pt_ma_table_create(float k_lo, float k_hi, int n_k, int n_z, pt_ma_table *out)
+{
+    if (!out) return PT_ERR_ARG;
+    *out = nullptr;
+    if (!(k_lo > 0.0f) || !(k_hi > k_lo) || n_k < 2 || n_k > 4096 || n_z < 2 || n_z > 65536) return PT_ERR_ARG;
+    pt_ma_table p = new pt_ma_table_s;
+    p->k_lo = k_lo;
+    p->k_hi = k_hi;
+    p->n_k = n_k;
+    p->n_z = n_z;
+    p->inv_dk = (float)((n_k - 1) / ((double)k_hi - (double)k_lo));
+    p->inv_dz = (float)((n_z - 1) / (1.0 + (double)k_hi));
+    p->d_tab = nullptr;
+    size_t cnt = (size_t)n_k * n_z;
+    cudaError_t e = cudaMalloc(&p->d_tab, cnt * sizeof(float4));
+    if (e == cudaSuccess) {
+        ma_table_kernel<<<(unsigned)((cnt + 255) / 256), 256>>>(k_lo, k_hi, n_k, n_z, p->d_tab);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(p->d_tab);
+        delete p;
+        return set_cuda_error(e, "pt_ma_table_create");
+    }
+    *out = p;
+    return PT_OK;
+}
+
+int pt_ma_table_destroy(pt_ma_table p)
+{
+    if (!p) return PT_OK;
+    cudaFree(p->d_tab);
+    delete p;
+    return PT_OK;
+}
+
+int pt_ma_terms_interp(pt_ma_table p, const float *k, const float *z, size_t n, float *le, float *ld, float *ed,
+                       pt_stream_t stream)
+{
+    if (!p) return PT_ERR_ARG;
+    if (n == 0) return PT_OK;
+    if (!k || !z) return PT_ERR_ARG;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffULL) return PT_ERR_ARG;
+    ma_terms_interp_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        p->d_tab, p->n_k, p->n_z, p->k_lo, p->k_hi, p->inv_dk, p->inv_dz, k, z, n, le, ld, ed);
+    return check_launch("pt_ma_terms_interp");
 }
 
 int pt_gim_plan_create(int N, int n_j, pt_gim_plan *out)
