@@ -87,6 +87,10 @@ def _lib():
                 ("pto_flux_quad_interp", _D, [_PD, _D, _D, _I, _I, _D, _D, _D, _D]),
                 ("pto_lc_ma_interp", _I, [_PD, _D, _D, _I, _I, _PD, _I, _PD, _PD, _PD, _PD, _PD, _PD, _I,
                                           _PD, _I, _PD, _I, _I, _D, _PD, _I]),
+                ("pto_gimenez_zi_table", None, [_I, _I, _D, _I, _I, _PD]),
+                ("pto_gimenez_zi_alpha", None, [_I, _I, _I, _D, _PD, _D, _PD]),
+                ("pto_lc_gimenez_zi", _I, [_PD, _I, _PD, _PD, _PD, _PD, _PD, _PD, _I, _PD, _I, _PD, _I, _I, _I,
+                                           _I, _I, _I, _D, _PD, _I]),
                 ("pto_mlp_nparams", _I, []),
                 ("pto_mlp_forward", None, [_PD, _PD, _I, _PD]),
                 ("pto_mlp_loss_grad", _D, [_PD, _PD, _PD, _I, _PD]),
@@ -304,6 +308,37 @@ def lc_gimenez(t, orbit, k, ld, n_j, n_ss=1, t_exp=0.0, n_threads=0):
     flux = np.zeros((n_v, n_b, t.size))
     nbad = _lib().pto_lc_gimenez(_ptr(t), t.size, _ptr(t0), _ptr(P), _ptr(a), _ptr(inc), _ptr(e), _ptr(w),
                                  n_v, _ptr(k), kpb, _ptr(ld), N, n_b, n_j, n_ss, t_exp, _ptr(flux), n_threads)
+    return flux, nbad
+
+
+def gimenez_zi_table(N, n_j, k, n_in, n_edge):
+    """alpha_0..alpha_N on the z nodes of the interpolated Gimenez model
+    (Sec. 3.3): [n_in + n_edge, N + 1]."""
+    tab = np.zeros((n_in + n_edge, N + 1))
+    _lib().pto_gimenez_zi_table(int(N), int(n_j), float(k), int(n_in), int(n_edge), _ptr(tab))
+    return tab
+
+
+def gimenez_zi_alpha(tab, k, z, n_in, n_edge):
+    tab = np.ascontiguousarray(tab, dtype=np.float64)
+    N = tab.shape[1] - 1
+    out = np.zeros(N + 1)
+    _lib().pto_gimenez_zi_alpha(N, int(n_in), int(n_edge), float(k), _ptr(tab), float(z), _ptr(out))
+    return out
+
+
+def lc_gimenez_zi(t, orbit, k, ld, n_j, n_in, n_edge, n_ss=1, t_exp=0.0, n_threads=0):
+    """lc_gimenez with the series read from z tables (Sec. 3.3)."""
+    t = _arr(t)
+    ld = np.ascontiguousarray(np.asarray(ld, dtype=np.float64))
+    n_v, n_b, N = ld.shape
+    t0, P, a, inc, e, w = _orbit(orbit, n_v)
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.float64))
+    kpb = 1 if k.ndim == 2 else 0
+    flux = np.zeros((n_v, n_b, t.size))
+    nbad = _lib().pto_lc_gimenez_zi(_ptr(t), t.size, _ptr(t0), _ptr(P), _ptr(a), _ptr(inc), _ptr(e), _ptr(w),
+                                    n_v, _ptr(k), kpb, _ptr(ld), N, n_b, n_j, int(n_in), int(n_edge), n_ss, t_exp,
+                                    _ptr(flux), n_threads)
     return flux, nbad
 
 

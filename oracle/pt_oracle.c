@@ -19,6 +19,7 @@
  *     recursion): the Gimenez series model.
  *   - Sec. 3.2: exposure supersampling.
  *   - Sec. 2.2.3: interpolation tables of the Mandel-Agol terms.
+ *   - Sec. 3.3: the Gimenez model interpolated in z.
  *   - Sec. 1: circular orbits and eccentric orbits solved with Newton's
  *     method (the paper names the solver but prints no formula).
  *   - Carlson (1995, Numer. Algorithms 10, 13): symmetric elliptic integrals
@@ -598,6 +599,108 @@ int pto_lc_gimenez(const double *t, int n_t, const double *t0, const double *P, 
     }
     return nbad;
 }
+
+/* ------------------------------------------------------------------------
+ * Gimenez model interpolated in z (Sec. 3.3).  The series is evaluated on
+ * n_in points over z in [0, zb], zb = max(1 - k, 0), and n_edge points over
+ * (zb, 1 + k]; light-curve points are read from these values by linear
+ * interpolation.  The tabulated values are alpha_0 .. alpha_N (free of limb
+ * darkening), so one table serves every passband; the flux is linear in the
+ * alpha_n, so this is the same as interpolating each passband's flux.
+ * Readings: linear interpolation; nodes
+ *   z_i = i zb / (n_in - 1),                 i = 0 .. n_in - 1,
+ *   z_{n_in + j} = zb + (j + 1)(1 + k - zb) / n_edge,   j = 0 .. n_edge - 1;
+ * out of transit (z >= 1 + k) alpha = 0.
+ * ---------------------------------------------------------------------- */
+static double zi_node(int i, int n_in, int n_edge, double k)
+{
+    double zb = (1.0 - k > 0.0) ? 1.0 - k : 0.0;
+    if (i < n_in) return i * zb / (n_in - 1);
+    return zb + (i - n_in + 1) * (1.0 + k - zb) / n_edge;
+}
+
+void pto_gimenez_zi_table(int N, int n_j, double k, int n_in, int n_edge, double *tab /* [n_in+n_edge][N+1] */)
+{
+    for (int i = 0; i < n_in + n_edge; ++i)
+        pto_gimenez_alpha(N, n_j, k, zi_node(i, n_in, n_edge, k), tab + (size_t)i * (N + 1));
+}
+
+void pto_gimenez_zi_alpha(int N, int n_in, int n_edge, double k, const double *tab, double z, double *alpha)
+{
+    z = fabs(z);
+    for (int n = 0; n <= N; ++n) alpha[n] = 0.0;
+    if (!(z < 1.0 + k)) return;
+    double zb = (1.0 - k > 0.0) ? 1.0 - k : 0.0;
+    int i0;
+    double w;
+    if (z <= zb && zb > 0.0) {
+        double f = z / (zb / (n_in - 1));
+        i0 = (int)floor(f);
+        if (i0 > n_in - 2) i0 = n_in - 2;
+        w = f - i0;
+    } else if (z <= zb) {   /* k >= 1: the first region is the single point z = 0 */
+        i0 = 0;
+        w = 0.0;
+    } else {
+        double f = (z - zb) / ((1.0 + k - zb) / n_edge);   /* 0 at node n_in - 1 */
+        int c = (int)floor(f);
+        if (c > n_edge - 1) c = n_edge - 1;
+        i0 = n_in - 1 + c;
+        w = f - c;
+    }
+    for (int n = 0; n <= N; ++n)
+        alpha[n] = (1.0 - w) * tab[(size_t)i0 * (N + 1) + n] + w * tab[(size_t)(i0 + 1) * (N + 1) + n];
+}
+
+int pto_lc_gimenez_zi(const double *t, int n_t, const double *t0, const double *P, const double *a,
+                      const double *inc, const double *e, const double *w, int n_v, const double *k,
+                      int k_per_band, const double *ld /* [v][b][N] */, int N, int n_b, int n_j, int n_in,
+                      int n_edge, int n_ss, double t_exp, double *flux /* [v][b][t] */, int n_threads)
+{
+    int nbad = 0;
+    int nz = n_in + n_edge;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#endif
+    for (int v = 0; v < n_v; ++v) {
+        double *tab = (double *)malloc(sizeof(double) * (size_t)nz * (N + 1) * n_b);
+        double alpha[64];
+        for (int b = 0; b < n_b; ++b) {
+            double kk = k_per_band ? k[(size_t)v * n_b + b] : k[v];
+            if (b == 0 || k_per_band)
+                pto_gimenez_zi_table(N, n_j, kk, n_in, n_edge, tab + (size_t)b * nz * (N + 1));
+        }
+        for (int i = 0; i < n_t; ++i) {
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] = 0.0;
+            for (int s = 0; s < n_ss; ++s) {
+                double tt = t[i] + t_exp * ((s + 0.5) / n_ss - 0.5);
+                int bad = 0;
+                double z = orbit_z(t0, P, a, inc, e, w, v, tt, &bad);
+                nbad += bad;
+                for (int b = 0; b < n_b; ++b) {
+                    double kk = k_per_band ? k[(size_t)v * n_b + b] : k[v];
+                    const double *tb = tab + (size_t)(k_per_band ? b : 0) * nz * (N + 1);
+                    pto_gimenez_zi_alpha(N, n_in, n_edge, kk, tb, z, alpha);
+                    const double *u = ld + ((size_t)v * n_b + b) * N;
+                    double su = 0.0, sd = 0.0;
+                    for (int n = 1; n <= N; ++n) {
+                        su += u[n - 1];
+                        sd += n * u[n - 1] / (n + 2.0);
+                    }
+                    double D = 1.0 - sd;
+                    double al = (1.0 - su) / D * alpha[0];
+                    for (int n = 1; n <= N; ++n) al += u[n - 1] / D * alpha[n];
+                    flux[((size_t)v * n_b + b) * n_t + i] += 1.0 - al;
+                }
+            }
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] /= n_ss;
+        }
+        free(tab);
+    }
+    return nbad;
+}
+
 
 /* Sum of squared residuals per (vector, passband): sum_t w (y - f)^2, the
  * likelihood reduction the paper moves onto the device (Sec. 3.4).
