@@ -337,6 +337,39 @@ def bench_ma_interp(pt, torch, dev, stream, K, flush, t, orb, k, ld, wl, f_exact
             "max_abs_diff_vs_exact": err, "gpu_launches_per_call": 2}
 
 
+def bench_gimenez_zi(pt, torch, dev, stream, K, flush, plan, t, orb, k, ldg, wl, f_series, n_in=64, n_edge=64):
+    """Gimenez model interpolated in z (Sec. 3.3) on the long-cadence
+    workload, timed like the series call, and its largest flux difference
+    from the series path."""
+    n_t, n_v = t.numel(), k.numel()
+    work = torch.empty(int(pt.load_library().pt_gimenez_zi_work_bytes(plan.handle, n_in, n_edge, n_t, n_v, 1, 0)),
+                       dtype=torch.uint8, device=dev)
+    f = torch.empty_like(f_series)
+
+    def run():
+        pt.gimenez_zi(plan, t, orb, k, ldg, n_in=n_in, n_edge=n_edge, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=work,
+                      flux=f)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(K):
+        flush.fill_(i & 0xff)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    m = float(np.mean(ms))
+    err = float((f.double() - f_series.double()).abs().max().item())
+    return {"workload": wl["name"], "grid": "n_in = %d, n_edge = %d" % (n_in, n_edge), "ms_per_call": m,
+            "value": n_t * n_v / (m * 1e-3), "unit": "flux points/s", "max_abs_diff_vs_series": err,
+            "gpu_launches_per_call": 6}
+
+
 def only_main(args):
     """One extra leg alone, at full or reduced size (profiler capture cases)."""
     import torch
@@ -554,9 +587,10 @@ def main():
                 "peak_source": "FP32 lanes 152 SM x 128 x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_max, peak_src),
                 "algorithmic_flops_per_launch": flops, "in_transit_evaluations": n_intr}
 
-    adjoint = batched = surrogate = ma_interp = None
+    adjoint = batched = surrogate = ma_interp = gim_zi = None
     if not args.no_extra:
         ma_interp = bench_ma_interp(pt, torch, dev, stream, K, flush, t, orb, k, ld, wl, fm)
+        gim_zi = bench_gimenez_zi(pt, torch, dev, stream, K, flush, plan, t, orb, k, ldg, wl, fg)
         adjoint = bench_adjoint(pt, torch, dev, stream, K, flush)
         batched = bench_batched(pt, torch, dev, stream, K, flush)
         surrogate = bench_surrogate(torch, dev, stream)
@@ -585,7 +619,7 @@ def main():
                            "parallelism": "replicas x%d" % ws},
                 "components_ms": {"ma_quad": float(np.mean(ma_ms)), "gimenez": g_mean_ms},
                 "max_abs_err_vs_oracle": max_err,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ma_interp": ma_interp, "adjoint": adjoint,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ma_interp": ma_interp, "gimenez_zi": gim_zi, "adjoint": adjoint,
                 "batched": batched, "surrogate": surrogate,
                 "gpu_launches": 7 * K, "clocks": dict(clocks, window="%.1f s of untimed steps + the timed region"
                                                       % args.heat_s) if clocks else None,

@@ -19,7 +19,7 @@ import os
 from . import build as _build_mod
 
 __all__ = ["load_library", "Orbit", "Theta", "orbit_to_device", "z_circ", "z_ecc", "ma_terms", "ma_quad",
-           "MATable", "ma_terms_interp", "ma_quad_interp",
+           "MATable", "ma_terms_interp", "ma_quad_interp", "gimenez_zi",
            "ma_quad_work_bytes", "GimenezPlan", "gimenez", "gimenez_alpha", "ma_quad_bwd", "transit_ssr",
            "PTError", "Z_BEHIND"]
 
@@ -87,6 +87,9 @@ def load_library(build_if_missing: bool = False):
         "pt_gimenez_work_bytes": (_c_size, [P, _c_int, _c_int, _c_int, _c_int]),
         "pt_gimenez": (_c_int, [P, P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int, _c_double,
                                 _c_int, P, P, P, P, P, _c_size, P, P]),
+        "pt_gimenez_zi_work_bytes": (_c_size, [P, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
+        "pt_gimenez_zi": (_c_int, [P, _c_int, _c_int, P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int,
+                                   _c_int, _c_double, _c_int, P, P, P, P, P, _c_size, P, P]),
         "pt_ma_quad_bwd_work_bytes": (_c_size, [_c_int]),
         "pt_ma_quad_bwd": (_c_int, [P, _c_int, ctypes.POINTER(Theta), _c_int, _c_double, _c_int, P, P, P, P, P, P,
                                     _c_size, P, P]),
@@ -344,6 +347,28 @@ def gimenez(plan, t, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None
     _check(lib.pt_gimenez(plan.handle, _ptr(t), n_t, ctypes.byref(o), _ptr(k), kpb, _ptr(ld), n_b, int(n_ss),
                           float(t_exp), int(max_iter), _ptr(y), _ptr(wt), _ptr(fl), _ptr(ss), _ptr(work),
                           work.numel(), _ptr(n_bad), _stream()), "pt_gimenez")
+    return fl, ss
+
+
+def gimenez_zi(plan, t, orb, k, ld, n_in=64, n_edge=64, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None,
+               want_flux=True, want_ssr=False, work=None, flux=None, ssr=None, n_bad=None):
+    """Gimenez light curves interpolated in z (pt_gimenez_zi, Sec. 3.3):
+    alpha_n on n_in nodes over [0, 1 - k] and n_edge over (1 - k, 1 + k]."""
+    torch = _torch()
+    lib = load_library()
+    o, n_v = _orbit_struct(orb)
+    n_b = int(ld.shape[1])
+    if int(ld.shape[2]) != plan.N:
+        raise PTError("ld has %d coefficients, plan expects %d" % (int(ld.shape[2]), plan.N))
+    kpb = 1 if k.dim() == 2 else 0
+    n_t = t.numel()
+    fl, ss = _lc_outputs(n_v, n_b, n_t, want_flux, want_ssr, t.device, flux, ssr)
+    need = int(lib.pt_gimenez_zi_work_bytes(plan.handle, int(n_in), int(n_edge), n_t, n_v, n_b, kpb))
+    if work is None or work.numel() < need:
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device=t.device)
+    _check(lib.pt_gimenez_zi(plan.handle, int(n_in), int(n_edge), _ptr(t), n_t, ctypes.byref(o), _ptr(k), kpb,
+                             _ptr(ld), n_b, int(n_ss), float(t_exp), int(max_iter), _ptr(y), _ptr(wt), _ptr(fl),
+                             _ptr(ss), _ptr(work), work.numel(), _ptr(n_bad), _stream()), "pt_gimenez_zi")
     return fl, ss
 
 

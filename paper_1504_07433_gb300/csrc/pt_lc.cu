@@ -668,6 +668,170 @@ __global__ void __launch_bounds__(GS_THREADS, GS_MIN_CTAS) gim_series_kernel(Gim
 
 size_t gim_series_smem(int N, int n_j) { return (size_t)(N + 1) * n_j * sizeof(float4); }
 
+// ---------------------------------------------------------------------------
+// Gimenez model interpolated in z (Sec. 3.3).  gim_zi_table_kernel evaluates
+// alpha_0..alpha_N of every geometry on its z nodes (n_in over [0, zb],
+// zb = max(1 - k, 0), then n_edge over (zb, 1 + k]) with the same Clenshaw
+// summation as the series kernel; gim_zi_kernel reads them by linear
+// interpolation for every listed (time, geometry) pair, with the same work
+// items, staging and passband combination as the series kernel.
+// ---------------------------------------------------------------------------
+constexpr int ZI_MAX_VALUES = 16384;   // (n_in + n_edge)(N + 1) per geometry
+
+struct ZiGrid {
+    float zb, h1, h2, inv_h1, inv_h2;
+};
+
+__device__ __forceinline__ ZiGrid zi_grid(float k, int n_in, int n_edge)
+{
+    ZiGrid q;
+    q.zb = fmaxf(1.0f - k, 0.0f);
+    q.h1 = q.zb / (float)(n_in - 1);
+    q.h2 = (1.0f + k - q.zb) / (float)n_edge;
+    q.inv_h1 = (q.zb > 0.0f) ? 1.0f / q.h1 : 0.0f;
+    q.inv_h2 = 1.0f / q.h2;
+    return q;
+}
+
+__global__ void __launch_bounds__(128) gim_zi_table_kernel(const GeomRec *rec, const float4 *gtab, int NP1, int n_j,
+                                                          int n_in, int n_edge, float *atab)
+{
+    const int g = blockIdx.x;
+    const int nz = n_in + n_edge;
+    const float kk = rec[g].k;
+    const ZiGrid G = zi_grid(kk, n_in, n_edge);
+    const float4 *tab = gtab + (size_t)g * NP1 * n_j;
+    const float bk = kk / (1.0f + kk);
+    const float b2 = bk * bk;
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) {
+        float z = (i < n_in) ? (float)i * G.h1 : G.zb + (float)(i - n_in + 1) * G.h2;
+        float x = 0.0f, q = 0.0f;
+        if (z < 1.0f + kk) {
+            float c = z / (1.0f + kk);
+            x = c * c;
+            q = sqrtf((1.0f - c) * (1.0f + c));
+        }
+        float *out = atab + ((size_t)g * nz + i) * NP1;
+        for (int n = 0; n < NP1; ++n) {
+            const float4 *tn = tab + (size_t)n * n_j;
+            float c1 = 0.0f, c2 = 0.0f;
+            for (int j = n_j - 1; j >= 0; --j) {
+                float4 c = tn[j];
+                float bj = fmaf(fmaf(c.y, x, c.x), c1, fmaf(c.z, c2, c.w));
+                c2 = c1;
+                c1 = bj;
+            }
+            float qq = q * q;
+            float pw = qq * qq;
+            for (int m = 0; m < n; ++m) pw *= q;
+            out[n] = (b2 * pw) * c1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GS_THREADS) gim_zi_kernel(GimArgs A, const float *atab, int n_in, int n_edge)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int NP1 = A.N + 1;
+    const int nz = n_in + n_edge;
+    float *stab = reinterpret_cast<float *>(dsm);   // [nz][N+1]
+    float *salpha = stab + nz * NP1;                // [N+1][GS_THREADS]
+    __shared__ GeomRec srec;
+    __shared__ int sitem, sgeom, sbad;
+
+    const int nss = A.n_ss;
+    const int tid = threadIdx.x;
+    const int total = A.pref[A.n_geom];
+    const float inv_nss = 1.0f / (float)nss;
+    int nbad = 0;
+    int staged = -1;
+    if (tid == 0) sbad = 0;
+
+#pragma unroll 1
+    for (;;) {
+        if (tid == 0) {
+            int it = atomicAdd(A.ctr, 1);
+            int g = -1;
+            if (it < total) {   // the largest g with pref[g] <= it
+                int lo = 0, hi = A.n_geom - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (A.pref[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                g = lo;
+            }
+            sitem = it;
+            sgeom = g;
+        }
+        __syncthreads();
+        const int it = sitem;
+        const int g = sgeom;
+        if (it >= total) break;   // uniform over the CTA
+        if (g != staged) {
+            const float *src = atab + (size_t)g * nz * NP1;
+            for (int i = tid; i < nz * NP1; i += GS_THREADS) stab[i] = src[i];
+            if (tid < 6) reinterpret_cast<float4 *>(&srec)[tid] = reinterpret_cast<const float4 *>(&A.rec[g])[tid];
+            staged = g;
+        }
+        for (int n = 0; n < NP1; ++n) salpha[n * GS_THREADS + tid] = 0.0f;
+        __syncthreads();
+        const int i = (it - A.pref[g]) * GS_THREADS + tid;
+        if (i < A.cnt[g]) {
+            const int t = A.list[(size_t)g * A.n_t + i];
+            float2 ts = A.tsplit[t];
+            float dt = pt::reduce_time(ts.x, ts.y, srec);
+            const float kk = srec.k;
+            const ZiGrid G = zi_grid(kk, n_in, n_edge);
+#pragma unroll 1
+            for (int s = 0; s < nss; ++s) {
+                bool bad = false;
+                float z = pt::orbit_z(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad);
+                if (bad) ++nbad;
+                if (!(z < 1.0f + kk)) continue;   // out of transit: alpha = 0
+                int i0;
+                float w;
+                if (z <= G.zb && G.zb > 0.0f) {
+                    float f = z * G.inv_h1;
+                    i0 = min((int)f, n_in - 2);
+                    w = f - (float)i0;
+                } else if (z <= G.zb) {            // k >= 1: the first region is z = 0
+                    i0 = 0;
+                    w = 0.0f;
+                } else {
+                    float f = (z - G.zb) * G.inv_h2;
+                    int c = min((int)f, n_edge - 1);
+                    i0 = n_in - 1 + c;
+                    w = f - (float)c;
+                }
+                const float *a0 = stab + i0 * NP1;
+                for (int n = 0; n < NP1; ++n)
+                    salpha[n * GS_THREADS + tid] += fmaf(w, a0[NP1 + n] - a0[n], a0[n]);
+            }
+#pragma unroll 1
+            for (int bb = 0; bb < A.n_bpg; ++bb) {
+                size_t row = (size_t)g * A.n_bpg + bb;
+                const float *u = A.ld + row * A.N;
+                // C_0 = (1 - sum u)/D, C_n = u_n/D, D = 1 - sum n u_n/(n+2)   (Sec. 2.1.3)
+                float su = 0.0f, sd = 0.0f;
+                for (int n = 1; n <= A.N; ++n) {
+                    float un = u[n - 1];
+                    su += un;
+                    sd += (float)n * un / (float)(n + 2);
+                }
+                float al = (1.0f - su) * salpha[tid];
+                for (int n = 1; n <= A.N; ++n) al = fmaf(u[n - 1], salpha[n * GS_THREADS + tid], al);
+                A.flux[row * A.n_t + t] = 1.0f - al / (1.0f - sd) * inv_nss;
+            }
+        }
+    }
+    if (nbad) atomicAdd(&sbad, nbad);
+    __syncthreads();
+    if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
+}
+
+size_t gim_zi_smem(int N, int nz) { return (size_t)(N + 1) * (nz + GS_THREADS) * sizeof(float); }
+
 // Double-float arithmetic for the table recursion: a value is the unevaluated
 // sum h + l of two floats (about 48 significant bits).  Sums and products
 // carry their rounding errors exactly (Knuth's two-sum; the FMA form of
@@ -945,10 +1109,11 @@ int check_orbit(const pt_orbit *orb, bool need_ecc)
 // work-item counter), work-item prefix, pair lists and a flux scratch used
 // when only residuals are asked for.
 struct WorkLayout {
-    size_t rec, tsplit, T, part, cnt, pref, list, fscr, total;
+    size_t rec, tsplit, T, part, cnt, pref, list, fscr, atab, total;
 };
 
-WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n_j)
+// n_zi > 0 adds the z tables of the interpolated Gimenez model.
+WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n_j, int n_zi = 0)
 {
     int n_geom = k_per_band ? n_v * n_b : n_v;
     int n_tiles = (n_t + TT - 1) / TT;
@@ -958,7 +1123,7 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
     off += align256((size_t)n_geom * sizeof(GeomRec));
     L.tsplit = off;
     off += align256((size_t)n_t * sizeof(float2));
-    L.T = L.part = L.cnt = L.pref = L.list = L.fscr = off;
+    L.T = L.part = L.cnt = L.pref = L.list = L.fscr = L.atab = off;
     if (NP1 == 0) {
         L.part = off;
         off += align256((size_t)n_v * n_b * n_tiles * sizeof(float));
@@ -973,6 +1138,8 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
         off += align256((size_t)n_geom * n_t * sizeof(int));
         L.fscr = off;
         off += align256((size_t)n_v * n_b * n_t * sizeof(float));
+        L.atab = off;
+        off += align256((size_t)n_geom * n_zi * NP1 * sizeof(float));
     }
     L.total = off;
     return L;
@@ -1048,6 +1215,28 @@ int launch_series(const GimArgs &A, size_t smem, size_t max_items, cudaStream_t 
     if (grid < 1) grid = 1;
     gim_series_kernel<SB><<<(unsigned)grid, GS_THREADS, smem, s>>>(A);
     return check_launch("gim_series_kernel");
+}
+
+int launch_zi(const GimArgs &A, const float *atab, int n_in, int n_edge, size_t smem, size_t max_items,
+              cudaStream_t s)
+{
+    static thread_local size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(gim_zi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return set_cuda_error(e, "gim_zi_kernel smem attribute");
+        configured = smem;
+    }
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gim_zi_kernel, GS_THREADS, smem);
+    if (e != cudaSuccess) return set_cuda_error(e, "gim_zi_kernel occupancy");
+    if (per_sm < 1) return pt_internal::set_error(PT_ERR_ARG, "gim_zi_kernel", "does not fit on an SM");
+    size_t grid = (size_t)n_sm * per_sm;
+    if (grid > max_items) grid = max_items;
+    if (grid < 1) grid = 1;
+    gim_zi_kernel<<<(unsigned)grid, GS_THREADS, smem, s>>>(A, atab, n_in, n_edge);
+    return check_launch("gim_zi_kernel");
 }
 
 }  // namespace
@@ -1379,18 +1568,26 @@ size_t pt_gimenez_work_bytes(pt_gim_plan plan, int n_t, int n_v, int n_b, int k_
     return work_layout(n_t, n_v, n_b, k_per_band, plan->N + 1, plan->n_j).total;
 }
 
-int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band,
-               const float *ld, int n_b, int n_ss, double t_exp, int max_iter, const float *y, const float *wt,
-               float *flux, float *ssr, void *work, size_t work_bytes, int *n_bad, pt_stream_t stream)
+}  // extern "C"
+
+// pt_gimenez (n_in == 0: the series for every pair) and pt_gimenez_zi (the
+// series on z nodes, read back by interpolation).
+static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t, int n_t, const pt_orbit *orb,
+                        const float *k, int k_per_band, const float *ld, int n_b, int n_ss, double t_exp,
+                        int max_iter, const float *y, const float *wt, float *flux, float *ssr, void *work,
+                        size_t work_bytes, int *n_bad, pt_stream_t stream)
 {
     if (!plan) return PT_ERR_ARG;
+    const bool zi = n_in > 0;
+    if (zi && (n_in < 2 || n_edge < 1 || (size_t)(n_in + n_edge) * (plan->N + 1) > (size_t)ZI_MAX_VALUES))
+        return PT_ERR_ARG;
     int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, max_iter, y, flux, ssr, work);
     if (st) return st;
     if (n_t == 0 || orb->n_v == 0) return PT_OK;
     const int NP1 = plan->N + 1;
-    WorkLayout L = work_layout(n_t, orb->n_v, n_b, k_per_band, NP1, plan->n_j);
+    WorkLayout L = work_layout(n_t, orb->n_v, n_b, k_per_band, NP1, plan->n_j, zi ? n_in + n_edge : 0);
     if (work_bytes < L.total) return PT_ERR_WORKSPACE;
-    const size_t smem = gim_series_smem(plan->N, plan->n_j);
+    const size_t smem = zi ? gim_zi_smem(plan->N, n_in + n_edge) : gim_series_smem(plan->N, plan->n_j);
     if (smem > 200 * 1024) return PT_ERR_ARG;
     const int n_geom = k_per_band ? orb->n_v * n_b : orb->n_v;
     const int n_tiles = (n_t + TT - 1) / TT;
@@ -1408,6 +1605,12 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
         rec, n_geom, plan->n_j, plan->d_A, plan->d_recb, plan->d_coef, T);
     st = check_launch("gim_table_kernel");
     if (st) return st;
+    float *atab = (float *)(wb + L.atab);
+    if (zi) {
+        gim_zi_table_kernel<<<n_geom, 128, 0, s>>>(rec, T, NP1, plan->n_j, n_in, n_edge, atab);
+        st = check_launch("gim_zi_table_kernel");
+        if (st) return st;
+    }
     GimArgs A;
     memset(&A, 0, sizeof(A));
     A.tsplit = tsplit;
@@ -1440,7 +1643,9 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
     // (two supersamples per two-lane FMA) with the least masked tail
     const int h = (A.ppi < GS_THREADS) ? (n_ss + 1) / 2 : n_ss;
     const size_t max_items = (size_t)n_geom * ((n_t + A.ppi - 1) / A.ppi);
-    if (h == 1)
+    if (zi)
+        st = launch_zi(A, atab, n_in, n_edge, smem, max_items, s);
+    else if (h == 1)
         st = launch_series<1>(A, smem, max_items, s);
     else if (h <= 2)
         st = launch_series<2>(A, smem, max_items, s);
@@ -1462,6 +1667,32 @@ int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, 
         st = check_launch("ssr_rows_kernel");
     }
     return st;
+}
+
+extern "C" {
+
+int pt_gimenez(pt_gim_plan plan, const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band,
+               const float *ld, int n_b, int n_ss, double t_exp, int max_iter, const float *y, const float *wt,
+               float *flux, float *ssr, void *work, size_t work_bytes, int *n_bad, pt_stream_t stream)
+{
+    return gimenez_impl(plan, 0, 0, t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux, ssr,
+                        work, work_bytes, n_bad, stream);
+}
+
+size_t pt_gimenez_zi_work_bytes(pt_gim_plan plan, int n_in, int n_edge, int n_t, int n_v, int n_b, int k_per_band)
+{
+    if (!plan || n_t < 0 || n_v < 0 || n_b < 1 || n_in < 2 || n_edge < 1) return 0;
+    return work_layout(n_t, n_v, n_b, k_per_band, plan->N + 1, plan->n_j, n_in + n_edge).total;
+}
+
+int pt_gimenez_zi(pt_gim_plan plan, int n_in, int n_edge, const double *t, int n_t, const pt_orbit *orb,
+                  const float *k, int k_per_band, const float *ld, int n_b, int n_ss, double t_exp, int max_iter,
+                  const float *y, const float *wt, float *flux, float *ssr, void *work, size_t work_bytes,
+                  int *n_bad, pt_stream_t stream)
+{
+    if (n_in < 2) return PT_ERR_ARG;
+    return gimenez_impl(plan, n_in, n_edge, t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux,
+                        ssr, work, work_bytes, n_bad, stream);
 }
 
 }  // extern "C"
