@@ -91,6 +91,8 @@ def _lib():
                 ("pto_gimenez_zi_alpha", None, [_I, _I, _I, _D, _PD, _D, _PD]),
                 ("pto_lc_gimenez_zi", _I, [_PD, _I, _PD, _PD, _PD, _PD, _PD, _PD, _I, _PD, _I, _PD, _I, _I, _I,
                                            _I, _I, _I, _D, _PD, _I]),
+                ("pto_lc_ma_khat", _I, [_PD, _I, _PD, _PD, _PD, _PD, _PD, _PD, _I, _PD, _PD, _I, _I, _D, _PD,
+                                        _I]),
                 ("pto_mlp_nparams", _I, []),
                 ("pto_mlp_forward", None, [_PD, _PD, _I, _PD]),
                 ("pto_mlp_loss_grad", _D, [_PD, _PD, _PD, _I, _PD]),
@@ -246,6 +248,20 @@ def lc_ma(t, orbit, k, ld, n_ss=1, t_exp=0.0, n_threads=0):
     flux = np.zeros((n_v, n_b, t.size))
     nbad = _lib().pto_lc_ma(_ptr(t), t.size, _ptr(t0), _ptr(P), _ptr(a), _ptr(inc), _ptr(e), _ptr(w), n_v,
                             _ptr(k), kpb, _ptr(ld), n_b, n_ss, t_exp, _ptr(flux), n_threads)
+    return flux, nbad
+
+
+def lc_ma_khat(t, orbit, k, ld, n_ss=1, t_exp=0.0, n_threads=0):
+    """Quadratic MA flux cube with per-passband k through the k^2 / k_hat^2
+    scaling of Sec. 3.5; k and ld are [n_v, n_b] and [n_v, n_b, 2]."""
+    t = _arr(t)
+    ld = np.ascontiguousarray(np.asarray(ld, dtype=np.float64))
+    n_v, n_b = ld.shape[0], ld.shape[1]
+    t0, P, a, inc, e, w = _orbit(orbit, n_v)
+    k = np.ascontiguousarray(np.broadcast_to(np.asarray(k, dtype=np.float64), (n_v, n_b)))
+    flux = np.zeros((n_v, n_b, t.size))
+    nbad = _lib().pto_lc_ma_khat(_ptr(t), t.size, _ptr(t0), _ptr(P), _ptr(a), _ptr(inc), _ptr(e), _ptr(w), n_v,
+                                 _ptr(k), _ptr(ld), n_b, n_ss, t_exp, _ptr(flux), n_threads)
     return flux, nbad
 
 

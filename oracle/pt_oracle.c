@@ -20,6 +20,7 @@
  *   - Sec. 3.2: exposure supersampling.
  *   - Sec. 2.2.3: interpolation tables of the Mandel-Agol terms.
  *   - Sec. 3.3: the Gimenez model interpolated in z.
+ *   - Sec. 3.5: per-passband radius ratios through the k^2 / k_hat^2 scaling.
  *   - Sec. 1: circular orbits and eccentric orbits solved with Newton's
  *     method (the paper names the solver but prints no formula).
  *   - Carlson (1995, Numer. Algorithms 10, 13): symmetric elliptic integrals
@@ -533,6 +534,47 @@ int pto_lc_ma(const double *t, int n_t, const double *t0, const double *P, const
                 }
             }
             for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] /= n_ss;
+        }
+    }
+    return nbad;
+}
+
+/* Per-passband radius ratios through the approximation of Sec. 3.5: the
+ * model is evaluated once with the mean radius ratio k_hat of the vector's
+ * passbands, and each passband's transit depth 1 - f is scaled by
+ * k_b^2 / k_hat^2.  Reading: the factor multiplies the depth (the flux
+ * deficit), k_hat is the arithmetic mean over the passbands. */
+int pto_lc_ma_khat(const double *t, int n_t, const double *t0, const double *P, const double *a,
+                   const double *inc, const double *e, const double *w, int n_v, const double *k /* [v][b] */,
+                   const double *ld /* [v][b][2] */, int n_b, int n_ss, double t_exp, double *flux /* [v][b][t] */,
+                   int n_threads)
+{
+    int nbad = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#endif
+    for (int v = 0; v < n_v; ++v) {
+        double kh = 0.0;
+        for (int b = 0; b < n_b; ++b) kh += k[(size_t)v * n_b + b];
+        kh /= n_b;
+        for (int i = 0; i < n_t; ++i) {
+            for (int b = 0; b < n_b; ++b) flux[((size_t)v * n_b + b) * n_t + i] = 0.0;
+            for (int s = 0; s < n_ss; ++s) {
+                double tt = t[i] + t_exp * ((s + 0.5) / n_ss - 0.5);
+                int bad = 0;
+                double z = orbit_z(t0, P, a, inc, e, w, v, tt, &bad);
+                nbad += bad;
+                for (int b = 0; b < n_b; ++b) {
+                    const double *u = ld + ((size_t)v * n_b + b) * 2;
+                    flux[((size_t)v * n_b + b) * n_t + i] += pto_flux_quad(kh, z, u[0], u[1]);
+                }
+            }
+            for (int b = 0; b < n_b; ++b) {
+                double kb = k[(size_t)v * n_b + b];
+                double f = flux[((size_t)v * n_b + b) * n_t + i] / n_ss;
+                flux[((size_t)v * n_b + b) * n_t + i] = 1.0 - (kb * kb) / (kh * kh) * (1.0 - f);
+            }
         }
     }
     return nbad;
