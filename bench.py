@@ -203,6 +203,21 @@ def bench_batched(pt, torch, dev, stream, K, flush, n_walkers=1024, modes=("ssr"
     plan.close()
     del plan
     torch.cuda.empty_cache()
+    # per-passband k through the k^2 / k_hat^2 scaling (Sec. 3.5): timed in
+    # SSR mode; its departure from per-passband k on a 16-walker flux cube
+    plan = pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, y=y, want_flux=False, want_ssr=True, autotune=True,
+                        k_mode=1)
+    m = timed(plan)
+    sub = {kk: (None if vv is None else vv[:16]) for kk, vv in orb.items()}
+    fe = pt.BatchPlan(t, wl["lc_offsets"], sub, k[:16].contiguous(), ld[:16].contiguous(), want_flux=True).run()[0]
+    fk = pt.BatchPlan(t, wl["lc_offsets"], sub, k[:16].contiguous(), ld[:16].contiguous(), want_flux=True,
+                      k_mode=1).run()[0]
+    err = float((fk.double() - fe.double()).abs().max().item())
+    out["khat_ssr_mode"] = dict(plan.info(), ms_per_call=m, value=pts / (m * 1e-3), unit="flux points/s",
+                                max_abs_diff_vs_per_band_k_16_walkers=err)
+    plan.close()
+    del plan, fe, fk
+    torch.cuda.empty_cache()
     if "cube" not in modes:
         return out
     plan = pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, want_flux=True, want_ssr=False, autotune=True)

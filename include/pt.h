@@ -256,6 +256,10 @@ typedef struct pt_batch_desc {
     float *flux;            /* [n_v][n_b][n_t] device or NULL */
     float *ssr;             /* [n_v][n_b] device or NULL (not both NULL) */
     int *n_bad;             /* optional device counter of non-converged Newton solves */
+    int k_mode;             /* 0: each passband with its own k (exact);
+                               1: the model once per walker with k_hat, the mean of its
+                                  passbands' k, and each passband's depth 1 - f scaled by
+                                  k_b^2 / k_hat^2 (Sec. 3.5) */
 } pt_batch_desc;
 
 typedef struct pt_batch_plan_s *pt_batch_plan;

@@ -57,6 +57,7 @@ struct BatchArgs {
     int n_items;
     int *counter;
     int *n_bad;
+    int khat;            // k_mode 1: terms once per time with k_hat (Sec. 3.5)
 };
 
 struct BatchSetupArgs {
@@ -69,6 +70,7 @@ struct BatchSetupArgs {
     float half_exp;
     GeomRec *rec;
     int n_vblocks;
+    int khat;
 };
 
 __global__ void batch_setup_kernel(BatchSetupArgs s)
@@ -76,8 +78,15 @@ __global__ void batch_setup_kernel(BatchSetupArgs s)
     if ((int)blockIdx.x < s.n_vblocks) {
         int v = blockIdx.x * blockDim.x + threadIdx.x;
         if (v >= s.orb.n_v) return;
-        float kmax = 0.0f;
-        for (int b = 0; b < s.n_b; ++b) kmax = fmaxf(kmax, s.k[(size_t)v * s.n_b + b]);
+        // the geometry's k: the largest passband k (its window covers every
+        // passband), or in k_hat mode the mean, the only k evaluated
+        float kmax = 0.0f, ksum = 0.0f;
+        for (int b = 0; b < s.n_b; ++b) {
+            float kb = s.k[(size_t)v * s.n_b + b];
+            kmax = fmaxf(kmax, kb);
+            ksum += kb;
+        }
+        if (s.khat) kmax = ksum / (float)s.n_b;
         bool ecc = s.orb.e != nullptr;
         pt::make_geom_rec(s.orb.t0[v], s.orb.P[v], s.orb.a[v], s.orb.inc[v], ecc, ecc ? s.orb.e[v] : 0.0f,
                           ecc ? s.orb.w[v] : 0.0f, kmax, s.half_exp, &s.rec[v]);
@@ -96,9 +105,10 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
 {
     extern __shared__ __align__(16) float dyn[];
     float *fbuf = dyn;                    // [n_b][TT]
-    float *swt = dyn + A.n_b * TT;        // [n_b][4]: we, wd, wn, k
+    float *swt = dyn + A.n_b * TT;        // [n_b][4]: we, wd, wn, k (k_hat mode: k^2 / k_hat^2)
     __shared__ GeomRec srec;
     __shared__ float sdt[TT], sz[TT];
+    __shared__ float ste[3][TT];          // k_hat mode: supersample-mean terms per time
     __shared__ unsigned char sflag[TT];
     __shared__ unsigned short squeue[TT];
     __shared__ int sqn, s_item, sbad;
@@ -124,7 +134,12 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
             swt[4 * b] = we;
             swt[4 * b + 1] = wd;
             swt[4 * b + 2] = wn;
-            swt[4 * b + 3] = A.k[(size_t)v * A.n_b + b];
+            float kb = A.k[(size_t)v * A.n_b + b];
+            if (A.khat) {
+                float r = kb / A.rec[v].k;
+                kb = r * r;
+            }
+            swt[4 * b + 3] = kb;
         }
         __syncthreads();
         // A: window test, z, compaction
@@ -146,7 +161,37 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
         const int nq = sqn;
         const int nu = nq * A.n_b;
         const float inv_ss = 1.0f / (float)A.n_ss;
-        for (int u = tid; u < nu; u += TT) {
+        if (A.khat) {
+            // the terms once per in-window time, with k_hat ...
+            for (int qi = tid; qi < nq; qi += TT) {
+                int tl = squeue[qi];
+                float le = 0.0f, ld = 0.0f, ed = 0.0f;
+                for (int s = 0; s < A.n_ss; ++s) {
+                    float zs = sz[tl];
+                    if (A.n_ss > 1) {
+                        float dts = sdt[tl] + A.t_exp * (((float)s + 0.5f) * inv_ss - 0.5f);
+                        zs = pt::orbit_z(srec, dts, A.max_iter, &bad);
+                    }
+                    float a0, a1, a2;
+                    pt::ma_terms(srec.k, zs, &a0, &a1, &a2);
+                    le += a0;
+                    ld += a1;
+                    ed += a2;
+                }
+                ste[0][tl] = le * inv_ss;
+                ste[1][tl] = ld * inv_ss;
+                ste[2][tl] = ed * inv_ss;
+            }
+            __syncthreads();
+            // ... then each passband's depth scaled by k_b^2 / k_hat^2
+            for (int u = tid; u < nu; u += TT) {
+                int b = u / nq, qi = u - b * nq;
+                int tl = squeue[qi];
+                float dep = swt[4 * b] * ste[0][tl] + swt[4 * b + 1] * ste[1][tl] + swt[4 * b + 2] * ste[2][tl];
+                fbuf[b * TT + tl] = 1.0f - swt[4 * b + 3] * dep;
+            }
+        }
+        for (int u = A.khat ? nu : tid; u < nu; u += TT) {
             int b = u / nq, qi = u - b * nq;
             int tl = squeue[qi];
             float kb = swt[4 * b + 3];
@@ -288,6 +333,7 @@ int enqueue(pt_batch_plan_s &p, cudaStream_t s)
     sa.tsplit = p.d_tsplit;
     sa.orb = d.orb;
     sa.k = d.k;
+    sa.khat = d.k_mode;
     sa.n_b = d.n_b;
     sa.half_exp = (float)(0.5 * d.t_exp);
     sa.rec = p.d_rec;
@@ -300,6 +346,7 @@ int enqueue(pt_batch_plan_s &p, cudaStream_t s)
     A.n_t = d.n_t;
     A.rec = p.d_rec;
     A.k = d.k;
+    A.khat = d.k_mode;
     A.ld = d.ld;
     A.n_v = d.orb.n_v;
     A.n_b = d.n_b;
@@ -383,6 +430,7 @@ int pt_batch_plan_create(const pt_batch_desc *d, int autotune, pt_batch_plan *ou
     if (!d->t || !d->lc_offsets || !o.t0 || !o.P || !o.a || !o.inc || !d->k || !d->ld) return PT_ERR_ARG;
     if ((o.e == nullptr) != (o.w == nullptr)) return PT_ERR_ARG;
     if (!d->flux && !d->ssr) return PT_ERR_ARG;
+    if (d->k_mode != 0 && d->k_mode != 1) return PT_ERR_ARG;
     if (d->ssr && !d->y) return PT_ERR_ARG;
     if (d->lc_offsets[0] != 0 || d->lc_offsets[d->n_lc] != d->n_t) return PT_ERR_ARG;
     for (int j = 0; j < d->n_lc; ++j)

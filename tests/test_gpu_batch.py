@@ -127,3 +127,34 @@ def test_batch_full_size_ssr_sampled(torch_cuda):
     # bound implied by the flux tolerance, plus FP32 accumulation
     bound = np.sum(2 * np.abs(yy[None] - ref) * TOL + TOL ** 2, axis=2) + 2e-5 * ssr_ref
     assert np.all(np.abs(s[np.ix_(vs, bs)] - ssr_ref) <= bound)
+
+
+@pytest.mark.parametrize("n_ss", [1, 3])
+def test_batch_khat_mode_vs_oracle(torch_cuda, n_ss):
+    """k_mode 1 (Sec. 3.5): one evaluation per walker with the mean k of its
+    passbands, each passband's depth scaled by k_b^2 / k_hat^2, against the
+    oracle's own k-hat model at 1e-6; its departure from per-passband k is the
+    approximation's, reported (and small for the workload's spread)."""
+    torch = torch_cuda
+    import paper_1504_07433_gb300 as pt
+    wl = W.batched(n_walkers=9, n_pb=7, n_lc=4, len_lo=150, len_hi=600)
+    wl["n_ss"] = n_ss
+    wl["t_exp"] = 0.004 if n_ss > 1 else 0.0
+    t, orb, k, ld = gpu_inputs(wl)
+    y = torch.as_tensor(wl["y"], dtype=torch.float32, device="cuda")
+    plan = pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, n_ss=n_ss, t_exp=wl["t_exp"], y=y, want_flux=True,
+                        want_ssr=True, k_mode=1)
+    flux, ssr = plan.run()
+    torch.cuda.synchronize()
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = oracle.lc_ma_khat(wl["t"], oracle_orbit(wl["orbit"]), f32(wl["k"]), f32(wl["ld"]), n_ss=n_ss,
+                            t_exp=wl["t_exp"])[0]
+    assert (ref < 1).mean() > 0.2
+    assert np.max(np.abs(f - ref)) <= TOL
+    yy = np.asarray(wl["y"], np.float32).astype(np.float64)
+    assert np.allclose(ssr.cpu().numpy(), np.sum((yy[None] - f) ** 2, axis=2), rtol=2e-5)
+    # the approximation against per-passband radius ratios
+    assert 0 < np.max(np.abs(f - _oracle(wl))) < 1e-3
+    # invalid mode refused
+    with pytest.raises(pt.PTError):
+        pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, want_flux=True, k_mode=2)
