@@ -370,12 +370,17 @@ __global__ void __launch_bounds__(TB) ma_bwd_kernel(BwdArgs A)
         // epoch and offset (double-float phase reduction)
         float s = ts.x - c.g.t0h;
         float n_ep = rintf(s * c.g.invP);
-        float dt = pt::reduce_time(ts.x, ts.y, c.g);
+        float dt = 0.0f;
+        bool inw = false;
+        if (pt::maybe_in_window(ts.x, c.g)) {
+            dt = pt::reduce_time(ts.x, ts.y, c.g);
+            inw = dt >= c.g.win_lo && dt <= c.g.win_hi;
+        }
         float f = 1.0f;
         float gp[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) gp[j] = 0.0f;
-        if (dt >= c.g.win_lo && dt <= c.g.win_hi) {
+        if (inw) {
             f = 0.0f;
             for (int ss = 0; ss < A.n_ss; ++ss) {
                 float dts = dt + A.t_exp * (((float)ss + 0.5f) * inv_ss - 0.5f);

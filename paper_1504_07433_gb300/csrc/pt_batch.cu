@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
         float dt = 0.0f, z = PT_ZBEHIND;
         if (tid < item.len) {
             float2 ts = A.tsplit[item.start + tid];
-            dt = pt::reduce_time(ts.x, ts.y, srec);
-            inw = dt >= srec.win_lo && dt <= srec.win_hi;
+            if (pt::maybe_in_window(ts.x, srec)) {
+                dt = pt::reduce_time(ts.x, ts.y, srec);
+                inw = dt >= srec.win_lo && dt <= srec.win_hi;
+            }
             if (inw && A.n_ss == 1) z = pt::orbit_z(srec, dt, A.max_iter, &bad);
         }
         sdt[tid] = dt;

@@ -55,6 +55,21 @@ __device__ __forceinline__ float reduce_time(float th, float tl, const GeomRec &
     return d + lo;
 }
 
+// First pass of the window test, in plain FP32: false only when t - t0 - nP
+// is certainly outside [win_lo, win_hi].  One FMA does the reduction with
+// the same epoch n as reduce_time; against the double-float result it drops
+// the rounding of s, the low parts of t, t0 and P and rounds once more, so
+// it is off by less than 2^-24 (|s| + |t_h| + |t0_h| + |n| P_h + |d|); the
+// margin doubles that (plus a nanosecond-scale floor).
+__device__ __forceinline__ bool maybe_in_window(float th, const GeomRec &r)
+{
+    float s = th - r.t0h;
+    float n = rintf(s * r.invP);
+    float d = fmaf(-n, r.Ph, s);
+    float m = 1.2e-7f * (fabsf(s) + fabsf(th) + fabsf(r.t0h) + fabsf(n) * r.Ph + fabsf(d)) + 1e-9f;
+    return (d + m >= r.win_lo) && (d - m <= r.win_hi);
+}
+
 // Projected separation z at time offset dt from conjunction (Sec. 1; the
 // paper prints no orbit formula).
 //   Circular:  phi = 2 pi dt / P,  z = a sqrt(sin^2 phi + cos^2 i cos^2 phi).

@@ -201,14 +201,16 @@ __device__ __forceinline__ void phase_a(const LcArgs &A, GeomRec *srec, float (*
         bool valid = tv && g < A.n_geom;
         float dt = 0.0f;
         bool inw = false;
-        if (valid) {
+        if (valid && pt::maybe_in_window(ts.x, srec[vl])) {
             dt = pt::reduce_time(ts.x, ts.y, srec[vl]);
             inw = (dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi);
         }
         sdt[vl][tl] = dt;
         sflag[vl][tl] = inw ? 1 : 0;
-        int slot = pt::warp_append(sqn, inw);
-        if (inw) squeue[slot] = (unsigned short)(vl * TT + tl);
+        if (__any_sync(0xffffffffu, inw)) {   // warp-uniform
+            int slot = pt::warp_append(sqn, inw);
+            if (inw) squeue[slot] = (unsigned short)(vl * TT + tl);
+        }
     }
     __syncthreads();
 }
@@ -387,13 +389,18 @@ __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A)
     unsigned inw_bits = 0u;
 #pragma unroll
     for (int vl = 0; vl < GW_VT; ++vl) {
-        bool inw = false;
-        if (tv && g0 + vl < A.n_geom) {
+        if (tv && g0 + vl < A.n_geom && pt::maybe_in_window(ts.x, srec[vl])) {
             float dt = pt::reduce_time(ts.x, ts.y, srec[vl]);
-            inw = (dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi);
+            if ((dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi)) inw_bits |= 1u << vl;
         }
-        slot[vl] = pt::warp_append(&scount[vl], inw);
-        if (inw) inw_bits |= 1u << vl;
+    }
+    // most warps have no pair in any window: skip the appends (warp-uniform)
+    if (__any_sync(0xffffffffu, inw_bits != 0u)) {
+#pragma unroll
+        for (int vl = 0; vl < GW_VT; ++vl) slot[vl] = pt::warp_append(&scount[vl], (inw_bits >> vl) & 1u);
+    } else {
+#pragma unroll
+        for (int vl = 0; vl < GW_VT; ++vl) slot[vl] = 0;
     }
     __syncthreads();
     if (tl < GW_VT) sbase[tl] = (scount[tl] > 0) ? atomicAdd(A.cnt + g0 + tl, scount[tl]) : 0;
