@@ -839,6 +839,85 @@ __global__ void __launch_bounds__(GS_THREADS) gim_zi_kernel(GimArgs A, const flo
 
 size_t gim_zi_smem(int N, int nz) { return (size_t)(N + 1) * (nz + GS_THREADS) * sizeof(float); }
 
+// ---------------------------------------------------------------------------
+// Mandel-Agol over the window kernel's pair lists: persistent CTAs take work
+// items of MA_PPI listed (time, geometry) pairs; each thread evaluates its
+// pair's supersamples (z, then lambda_e, lambda_d + 2/3 Theta, eta_d), sums
+// them in order and writes every passband's flux (Eq. ma_model).
+// ---------------------------------------------------------------------------
+constexpr int MA_PPI = 64;   // pairs per work item (= threads per CTA)
+
+__global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
+{
+    __shared__ GeomRec srec;
+    __shared__ int sitem, sgeom, sbad;
+    const int tid = threadIdx.x;
+    const int nss = A.n_ss;
+    const int total = A.pref[A.n_geom];
+    const float inv_nss = 1.0f / (float)nss;
+    int nbad = 0;
+    int staged = -1;
+    if (tid == 0) sbad = 0;
+#pragma unroll 1
+    for (;;) {
+        if (tid == 0) {
+            int it = atomicAdd(A.ctr, 1);
+            int g = -1;
+            if (it < total) {   // the largest g with pref[g] <= it
+                int lo = 0, hi = A.n_geom - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (A.pref[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                g = lo;
+            }
+            sitem = it;
+            sgeom = g;
+        }
+        __syncthreads();
+        const int it = sitem;
+        const int g = sgeom;
+        if (it >= total) break;   // uniform over the CTA
+        if (g != staged) {
+            if (tid < 6) reinterpret_cast<float4 *>(&srec)[tid] = reinterpret_cast<const float4 *>(&A.rec[g])[tid];
+            staged = g;
+        }
+        __syncthreads();
+        const int i = (it - A.pref[g]) * MA_PPI + tid;
+        if (i < A.cnt[g]) {
+            const int t = A.list[(size_t)g * A.n_t + i];
+            float2 ts = A.tsplit[t];
+            float dt = pt::reduce_time(ts.x, ts.y, srec);
+            float le = 0.0f, ld = 0.0f, ed = 0.0f;
+#pragma unroll 1
+            for (int s = 0; s < nss; ++s) {
+                bool bad = false;
+                float z = pt::orbit_z(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad);
+                if (bad) ++nbad;
+                float a0, a1, a2;
+                pt::ma_terms(srec.k, z, &a0, &a1, &a2);
+                le += a0;
+                ld += a1;
+                ed += a2;
+            }
+            le *= inv_nss;
+            ld *= inv_nss;
+            ed *= inv_nss;
+#pragma unroll 1
+            for (int bb = 0; bb < A.n_bpg; ++bb) {
+                size_t row = (size_t)g * A.n_bpg + bb;
+                float we, wd, wn;
+                pt::ma_weights(A.ld[row * 2], A.ld[row * 2 + 1], &we, &wd, &wn);
+                A.flux[row * A.n_t + t] = 1.0f - (we * le + wd * ld + wn * ed);
+            }
+        }
+    }
+    if (nbad) atomicAdd(&sbad, nbad);
+    __syncthreads();
+    if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
+}
+
 // Double-float arithmetic for the table recursion: a value is the unevaluated
 // sum h + l of two floats (about 48 significant bits).  Sums and products
 // carry their rounding errors exactly (Knuth's two-sum; the FMA form of
@@ -1152,6 +1231,16 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
     return L;
 }
 
+// pt_ma_quad runs over the window kernel's pair lists (the list layout: no
+// Gimenez tables); the tile kernel serves the interpolated and the
+// allocation-free variants.
+constexpr bool MA_LIST = true;
+
+size_t ma_list_work_bytes(int n_t, int n_v, int n_b, int k_per_band)
+{
+    return work_layout(n_t, n_v, n_b, k_per_band, 1, 0).total;
+}
+
 }  // namespace
 
 struct pt_ma_table_s {
@@ -1329,7 +1418,8 @@ static int lc_common_check(const double *t, int n_t, const pt_orbit *orb, const 
 size_t pt_ma_quad_work_bytes(int n_t, int n_v, int n_b, int k_per_band)
 {
     if (n_t < 0 || n_v < 0 || n_b < 1) return 0;
-    return work_layout(n_t, n_v, n_b, k_per_band, 0, 0).total;
+    size_t tile = work_layout(n_t, n_v, n_b, k_per_band, 0, 0).total;
+    return MA_LIST ? ma_list_work_bytes(n_t, n_v, n_b, k_per_band) : tile;
 }
 
 static int launch_setup(const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band, int n_b,
@@ -1361,6 +1451,72 @@ static int launch_setup(const double *t, int n_t, const pt_orbit *orb, const flo
 }
 
 }  // extern "C"
+
+// pt_ma_quad over the pair lists (window kernel, scan, ma_pairs_kernel).
+static int ma_quad_list(const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band,
+                        const float *ld, int n_b, int n_ss, double t_exp, int max_iter, const float *y,
+                        const float *wt, float *flux, float *ssr, void *work, size_t work_bytes, int *n_bad,
+                        pt_stream_t stream)
+{
+    int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, max_iter, y, flux, ssr, work);
+    if (st) return st;
+    if (n_t == 0 || orb->n_v == 0) return PT_OK;
+    WorkLayout L = work_layout(n_t, orb->n_v, n_b, k_per_band, 1, 0);
+    if (work_bytes < L.total) return PT_ERR_WORKSPACE;
+    const int n_geom = k_per_band ? orb->n_v * n_b : orb->n_v;
+    const int n_tiles = (n_t + TT - 1) / TT;
+    const int gy = (n_geom + GW_VT - 1) / GW_VT;
+    if (gy > 65535) return PT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *wb = (char *)work;
+    GeomRec *rec = (GeomRec *)(wb + L.rec);
+    float2 *tsplit = (float2 *)(wb + L.tsplit);
+    int *cnt = (int *)(wb + L.cnt);
+    st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, cnt, s);
+    if (st) return st;
+    GimArgs A;
+    memset(&A, 0, sizeof(A));
+    A.tsplit = tsplit;
+    A.n_t = n_t;
+    A.rec = rec;
+    A.n_geom = n_geom;
+    A.ld = ld;
+    A.N = 2;
+    A.n_bpg = k_per_band ? 1 : n_b;
+    A.n_ss = n_ss;
+    A.t_exp = (float)t_exp;
+    A.max_iter = max_iter;
+    A.flux = flux ? flux : (float *)(wb + L.fscr);
+    A.cnt = cnt;
+    A.pref = (int *)(wb + L.pref);
+    A.ctr = cnt + n_geom;
+    A.list = (int *)(wb + L.list);
+    A.ppi = MA_PPI;
+    A.n_bad = n_bad;
+    gim_window_kernel<<<dim3(n_tiles, gy), TT, 0, s>>>(A);
+    st = check_launch("gim_window_kernel");
+    if (st) return st;
+    gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, MA_PPI, A.pref, A.ctr);
+    st = check_launch("gim_scan_kernel");
+    if (st) return st;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ma_pairs_kernel, MA_PPI, 0);
+    if (e != cudaSuccess) return set_cuda_error(e, "ma_pairs_kernel occupancy");
+    size_t grid = (size_t)n_sm * (per_sm > 0 ? per_sm : 1);
+    const size_t max_items = (size_t)n_geom * ((n_t + MA_PPI - 1) / MA_PPI);
+    if (grid > max_items) grid = max_items;
+    if (grid < 1) grid = 1;
+    ma_pairs_kernel<<<(unsigned)grid, MA_PPI, 0, s>>>(A);
+    st = check_launch("ma_pairs_kernel");
+    if (st) return st;
+    if (ssr) {
+        ssr_rows_kernel<<<orb->n_v * n_b, 256, 0, s>>>(A.flux, y, wt, n_t, n_b, ssr);
+        st = check_launch("ssr_rows_kernel");
+    }
+    return st;
+}
 
 // pt_ma_quad and pt_ma_quad_interp: exact terms when tab is null, else the
 // interpolated ones.
@@ -1432,6 +1588,9 @@ int pt_ma_quad(const double *t, int n_t, const pt_orbit *orb, const float *k, in
                int n_b, int n_ss, double t_exp, int max_iter, const float *y, const float *wt, float *flux,
                float *ssr, void *work, size_t work_bytes, int *n_bad, pt_stream_t stream)
 {
+    if (MA_LIST)
+        return ma_quad_list(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux, ssr, work,
+                            work_bytes, n_bad, stream);
     return ma_quad_impl(nullptr, t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux, ssr,
                         work, work_bytes, n_bad, stream);
 }
@@ -1756,7 +1915,8 @@ extern "C" int pt_ma_quad_noalloc(const double *t, int n_t, const pt_orbit *orb,
                                   pt_stream_t stream)
 {
     if (!orb || n_t < 0 || orb->n_v < 0 || n_b < 1) return PT_ERR_ARG;
-    size_t need = pt_ma_quad_work_bytes(n_t, orb->n_v, n_b, k_per_band);
+    // the tile kernel: its scratch is small (records, time split, partials)
+    size_t need = work_layout(n_t, orb->n_v, n_b, k_per_band, 0, 0).total;
     if (need > (size_t)PT_MA_NOALLOC_SCRATCH_BYTES) {
         snprintf(g_last_error, sizeof(g_last_error),
                  "pt_ma_quad_noalloc: this problem needs %zu bytes of scratch, the static scratch holds %zu; "
@@ -1768,6 +1928,6 @@ extern "C" int pt_ma_quad_noalloc(const double *t, int n_t, const pt_orbit *orb,
     if (st) return st;
     // Every scratch byte the kernels read is written earlier in the same call
     // (geometry records, time split, residual partials), so nothing is cleared.
-    return pt_ma_quad(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux, ssr, scratch,
-                      (size_t)PT_MA_NOALLOC_SCRATCH_BYTES, n_bad, stream);
+    return ma_quad_impl(nullptr, t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, wt, flux, ssr,
+                        scratch, (size_t)PT_MA_NOALLOC_SCRATCH_BYTES, n_bad, stream);
 }
