@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 // Every pair's flux is computed by the same threads in the same order
 // whatever CTA takes its item, so the result is deterministic.
 // ---------------------------------------------------------------------------
-constexpr int GW_VT = 8;          // geometries per CTA of the window kernel
+constexpr int GW_VT = 32;         // geometries per CTA of the window kernel (<= 32: one bit each)
 constexpr int GS_THREADS = 128;   // threads per CTA of the series kernel
 constexpr int GS_MIN_CTAS = 6;    // resident CTAs per SM the register budget is sized for
 constexpr int G_MAX_NP1 = 17;     // N <= 16
@@ -366,53 +366,102 @@ struct GimArgs {
     int *n_bad;
 };
 
-// Pairs are counted per CTA in shared memory first, then one global atomic
-// per geometry reserves the CTA's stretch of that geometry's list.
+// One CTA covers TT times x GW_VT geometries.  The first pass of the window
+// test (as pt::maybe_in_window, but with its margin bounded once per tile and
+// geometry from the tile's largest |t_h|) costs a subtraction, a product, a
+// rounding, an FMA and two comparisons per pair against constants staged in
+// shared memory; candidates then take the exact double-float test.  Appends
+// in two passes over a per-thread bit mask: ballots count each warp's pairs
+// per geometry, one global atomic per geometry reserves the CTA's stretch of
+// its list, and the same ballots place every pair (warp order, then lane
+// order) inside that stretch.  Every other pair gets flux 1.
 __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A)
 {
+    constexpr int NW = TT / 32;
     __shared__ GeomRec srec[GW_VT];
-    __shared__ int scount[GW_VT], sbase[GW_VT];
-    const int tl = threadIdx.x;
-    for (int i = tl; i < GW_VT * 6; i += TT) {
+    __shared__ float4 stest[GW_VT];   // t0_h, 1/P, P_h, win_lo - m
+    __shared__ float shi[GW_VT];      // win_hi + m
+    __shared__ int swc[NW][GW_VT];    // pairs per (warp, geometry), then the warp's offset
+    __shared__ int sbase[GW_VT];
+    __shared__ float swmax[NW];
+    const int tl = threadIdx.x, lane = tl & 31, warp = tl >> 5;
+    const int g0 = blockIdx.y * GW_VT;
+    const int ng = min(GW_VT, A.n_geom - g0);
+    for (int i = tl; i < ng * 6; i += TT) {
         int vl = i / 6, c = i % 6;
-        int g = blockIdx.y * GW_VT + vl;
-        if (g < A.n_geom)
-            reinterpret_cast<float4 *>(&srec[vl])[c] = reinterpret_cast<const float4 *>(&A.rec[g])[c];
+        reinterpret_cast<float4 *>(&srec[vl])[c] = reinterpret_cast<const float4 *>(&A.rec[g0 + vl])[c];
     }
-    if (tl < GW_VT) scount[tl] = 0;
-    __syncthreads();
     const int t = blockIdx.x * TT + tl;
     const bool tv = t < A.n_t;
     const float2 ts = tv ? A.tsplit[t] : make_float2(0.0f, 0.0f);
-    const int g0 = blockIdx.y * GW_VT;
-    int slot[GW_VT];
-    unsigned inw_bits = 0u;
-#pragma unroll
-    for (int vl = 0; vl < GW_VT; ++vl) {
-        if (tv && g0 + vl < A.n_geom && pt::maybe_in_window(ts.x, srec[vl])) {
-            float dt = pt::reduce_time(ts.x, ts.y, srec[vl]);
-            if ((dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi)) inw_bits |= 1u << vl;
+    // the tile's largest |t_h| (non-negative floats order like their bits)
+    float am = __int_as_float(__reduce_max_sync(0xffffffffu, __float_as_int(fabsf(ts.x))));
+    if (lane == 0) swmax[warp] = am;
+    __syncthreads();
+    if (tl < ng) {
+        float tmax = swmax[0];
+        for (int w = 1; w < NW; ++w) tmax = fmaxf(tmax, swmax[w]);
+        const GeomRec &r = srec[tl];
+        // the margin of pt::maybe_in_window with |s| <= |t_h| + |t0_h|,
+        // |n| P_h <= |s| + P_h / 2 and |d| <= P_h / 2
+        float m = 1.2e-7f * (3.0f * tmax + 3.0f * fabsf(r.t0h) + r.Ph) + 1e-9f;
+        stest[tl] = make_float4(r.t0h, r.invP, r.Ph, r.win_lo - m);
+        shi[tl] = r.win_hi + m;
+    }
+    __syncthreads();
+    unsigned bits = 0u;
+    if (tv) {
+        const float th = ts.x;
+#pragma unroll 8
+        for (int vl = 0; vl < ng; ++vl) {
+            float4 q = stest[vl];
+            float sv = th - q.x;
+            float d = fmaf(-rintf(sv * q.y), q.z, sv);
+            if (d >= q.w && d <= shi[vl]) {   // candidate: the exact test
+                float dt = pt::reduce_time(th, ts.y, srec[vl]);
+                if ((dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi)) bits |= 1u << vl;
+            }
         }
     }
-    // most warps have no pair in any window: skip the appends (warp-uniform)
-    if (__any_sync(0xffffffffu, inw_bits != 0u)) {
-#pragma unroll
-        for (int vl = 0; vl < GW_VT; ++vl) slot[vl] = pt::warp_append(&scount[vl], (inw_bits >> vl) & 1u);
-    } else {
-#pragma unroll
-        for (int vl = 0; vl < GW_VT; ++vl) slot[vl] = 0;
+    const bool any = __any_sync(0xffffffffu, bits != 0u);
+    if (any) {
+        for (int vl = 0; vl < ng; ++vl) {
+            unsigned mb = __ballot_sync(0xffffffffu, (bits >> vl) & 1u);
+            if (lane == 0) swc[warp][vl] = __popc(mb);
+        }
+    } else if (lane < GW_VT) {
+        swc[warp][lane] = 0;
     }
     __syncthreads();
-    if (tl < GW_VT) sbase[tl] = (scount[tl] > 0) ? atomicAdd(A.cnt + g0 + tl, scount[tl]) : 0;
+    if (tl < ng) {   // per geometry: warp offsets, then one reservation
+        int run = 0;
+        for (int w = 0; w < NW; ++w) {
+            int c = swc[w][tl];
+            swc[w][tl] = run;
+            run += c;
+        }
+        sbase[tl] = run > 0 ? atomicAdd(A.cnt + g0 + tl, run) : 0;
+    }
     __syncthreads();
-#pragma unroll
-    for (int vl = 0; vl < GW_VT; ++vl) {
-        const int g = g0 + vl;
-        if (g >= A.n_geom) break;   // uniform over the CTA
-        if (inw_bits & (1u << vl)) {
-            A.list[(size_t)g * A.n_t + sbase[vl] + slot[vl]] = t;
-        } else if (tv) {
-            for (int bb = 0; bb < A.n_bpg; ++bb) A.flux[((size_t)g * A.n_bpg + bb) * A.n_t + t] = 1.0f;
+    if (any) {
+        const unsigned lt = (1u << lane) - 1u;
+        for (int vl = 0; vl < ng; ++vl) {
+            const bool in = (bits >> vl) & 1u;
+            unsigned mb = __ballot_sync(0xffffffffu, in);
+            if (in) A.list[(size_t)(g0 + vl) * A.n_t + sbase[vl] + swc[warp][vl] + __popc(mb & lt)] = t;
+        }
+    }
+    if (tv) {
+        const size_t row_stride = (size_t)A.n_t;
+        float *fp = A.flux + (size_t)g0 * A.n_bpg * row_stride + t;
+        if (A.n_bpg == 1) {
+#pragma unroll 8
+            for (int vl = 0; vl < ng; ++vl, fp += row_stride)
+                if (!((bits >> vl) & 1u)) *fp = 1.0f;
+        } else {
+            for (int vl = 0; vl < ng; ++vl)
+                for (int bb = 0; bb < A.n_bpg; ++bb, fp += row_stride)
+                    if (!((bits >> vl) & 1u)) *fp = 1.0f;
         }
     }
 }

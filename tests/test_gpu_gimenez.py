@@ -154,3 +154,31 @@ def test_gimenez_full_long_cadence_sampled(torch_cuda):
                    k=wl["k"][[v]], ld_gim=wl["ld_gim"][[v]], n_ss=wl["n_ss"], t_exp=wl["t_exp"])
         ref = _oracle_lc(sub, 128)
         assert np.max(np.abs(row[pick].astype(np.float64) - ref[0, 0])) <= TOL, v
+
+
+@pytest.mark.parametrize("order", ["shuffled", "partly_reversed"])
+def test_time_order_does_not_matter(torch_cuda, order):
+    """The window kernel searches sorted tiles by epoch and tests every pair
+    of unsorted ones; both give the oracle's light curves (MA and Gimenez)."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=4, n_t=2000, n_ss=3, cadence=0.01)
+    rng = np.random.default_rng(21)
+    if order == "shuffled":
+        perm = rng.permutation(wl["t"].size)
+    else:   # sorted tiles, one reversed stretch, and a tile mixing both
+        perm = np.arange(wl["t"].size)
+        perm[700:1300] = perm[700:1300][::-1]
+    wl["t"] = wl["t"][perm]
+    wl_g = dict(wl, ld=wl["ld_gim"])
+    t, orb, k, ld = gpu_inputs(wl)
+    ldg = torch.as_tensor(np.asarray(wl["ld_gim"], np.float32), device="cuda")
+    fm, _ = pt.ma_quad(t, orb, k, ld, n_ss=3, t_exp=wl["t_exp"])
+    plan = pt.GimenezPlan(8, 64)
+    fg, _ = pt.gimenez(plan, t, orb, k, ldg, n_ss=3, t_exp=wl["t_exp"])
+    ref_m = oracle.lc_ma(wl["t"], oracle_orbit(wl["orbit"]), f32(wl["k"]), f32(wl["ld"]), n_ss=3,
+                         t_exp=wl["t_exp"])[0]
+    ref_g = _oracle_lc(wl_g, 64)
+    assert (ref_m < 1).sum() > 0
+    assert np.max(np.abs(fm.cpu().numpy() - ref_m)) <= TOL
+    assert np.max(np.abs(fg.cpu().numpy() - ref_g)) <= TOL
