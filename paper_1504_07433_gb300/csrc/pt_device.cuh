@@ -121,6 +121,15 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
     return sqrtf(fmaf(U, U, Vi * Vi));
 }
 
+// Square root through the hardware reciprocal square root (about one ulp
+// off the correctly rounded value; exact zero at 0).  The Mandel-Agol terms
+// use it, and __fdividef, where their arguments are bounded well inside the
+// normal range; the accuracy budget of those terms is ~1e-7 absolute.
+__device__ __forceinline__ float fast_sqrt(float x)
+{
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 // ---------------------------------------------------------------------------
 // Bulirsch's general complete elliptic integral (Bulirsch 1969, Numer. Math.
 // 13, 305),
@@ -137,7 +146,7 @@ __device__ __forceinline__ void cel2(float kc, float a1, float b1, float rho, fl
                                      float *r2)
 {
     float p1 = 1.0f;
-    float p2 = sqrtf(rho);
+    float p2 = fast_sqrt(rho);
     float b2 = 0.0f;
     float m = 1.0f, e = kc;
 #pragma unroll 1
@@ -157,11 +166,11 @@ __device__ __forceinline__ void cel2(float kc, float a1, float b1, float rho, fl
         g = m;
         m = kc + m;
         if (fabsf(g - kc) <= g * 3e-4f) break;
-        kc = 2.0f * sqrtf(e);
+        kc = 2.0f * fast_sqrt(e);
         e = kc * m;
     }
-    *r1 = (0.5f * PT_PI_F) * fmaf(a1, m, b1) / (m * (m + p1));
-    *r2 = (0.5f * PT_PI_F) * fmaf(a2, m, b2) / (m * (m + p2));
+    *r1 = __fdividef((0.5f * PT_PI_F) * fmaf(a1, m, b1), m * (m + p1));
+    *r2 = __fdividef((0.5f * PT_PI_F) * fmaf(a2, m, b2), m * (m + p2));
 }
 
 // ---------------------------------------------------------------------------
@@ -216,7 +225,7 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
     // lens geometry: only the partial (and contact) cases need it
     float le_part = p2, eta1 = eta2;
     if (!inside) {
-        float fa = sqrtf(fmaxf(0.0f, oma * bm1));       // 4 x triangle area
+        float fa = fast_sqrt(oma * bm1);                 // 4 x triangle area
         float k1 = atan2f(fa, 1.0f - p2 + z2);
         float k0 = atan2f(fa, p2 + z2 - 1.0f);
         le_part = (p2 * k0 + k1 - 0.5f * fa) * (1.0f / pi);
@@ -256,19 +265,19 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
             e_out = eta1;
         }
     } else if (inside) {                             // cases 3, 9: lambda_2
-        kc = sqrtf(-bm1 / oma);
-        cKp = bm1 * (p2 * p - p2 * z - p * z2 + 2.0f * p + z2 * z - 4.0f * z) / (p + z);
+        kc = fast_sqrt(__fdividef(-bm1, oma));
+        cKp = __fdividef(bm1 * (p2 * p - p2 * z - p * z2 + 2.0f * p + z2 * z - 4.0f * z), p + z);
         cE = oma * (z2 + 7.0f * p2 - 4.0f);
-        rho = b / a;
-        cR = -12.0f * q * z * p / (a * b);
-        pref = 2.0f / (9.0f * pi * sqrtf(oma));
+        rho = __fdividef(b, a);
+        cR = __fdividef(-12.0f * q * z * p, a * b);
+        pref = __fdividef(2.0f, 9.0f * pi * fast_sqrt(oma));
     } else {                                         // cases 2, 8: lambda_1
-        kc = sqrtf(bm1 / (4.0f * z * p));
+        kc = fast_sqrt(__fdividef(bm1, 4.0f * z * p));
         cKp = -bm1 * (6.0f * p2 + 2.0f * p * z - 3.0f);
         cE = 4.0f * p * z * (z2 + 7.0f * p2 - 4.0f);
-        rho = 1.0f / a;
-        cR = -3.0f * q * oma / a;
-        pref = 1.0f / (9.0f * pi * sqrtf(p * z));
+        rho = __fdividef(1.0f, a);
+        cR = __fdividef(-3.0f * q * oma, a);
+        pref = __fdividef(1.0f, 9.0f * pi * fast_sqrt(p * z));
     }
     float lam = cst;
     if (need_cel) {
