@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
                 dt = pt::reduce_time(ts.x, ts.y, srec);
                 inw = dt >= srec.win_lo && dt <= srec.win_hi;
             }
-            if (inw && A.n_ss == 1) z = pt::orbit_z(srec, dt, A.max_iter, &bad);
+            if (inw && A.n_ss == 1) z = pt::orbit_z<true>(srec, dt, A.max_iter, &bad);
         }
         sdt[tid] = dt;
         sz[tid] = z;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
                     float zs = sz[tl];
                     if (A.n_ss > 1) {
                         float dts = sdt[tl] + A.t_exp * (((float)s + 0.5f) * inv_ss - 0.5f);
-                        zs = pt::orbit_z(srec, dts, A.max_iter, &bad);
+                        zs = pt::orbit_z<true>(srec, dts, A.max_iter, &bad);
                     }
                     float a0, a1, a2;
                     pt::ma_terms(srec.k, zs, &a0, &a1, &a2);
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
                 le = ld = ed = 0.0f;
                 for (int s = 0; s < A.n_ss; ++s) {
                     float dts = sdt[tl] + A.t_exp * (((float)s + 0.5f) * inv_ss - 0.5f);
-                    float zs = pt::orbit_z(srec, dts, A.max_iter, &bad);
+                    float zs = pt::orbit_z<true>(srec, dts, A.max_iter, &bad);
                     float a0, a1, a2;
                     pt::ma_terms(kb, zs, &a0, &a1, &a2);
                     le += a0;

@@ -55,6 +55,15 @@ __device__ __forceinline__ float reduce_time(float th, float tl, const GeomRec &
     return d + lo;
 }
 
+// Square root through the hardware reciprocal square root (about one ulp
+// off the correctly rounded value; exact zero at 0).  The Mandel-Agol terms
+// use it, and __fdividef, where their arguments are bounded well inside the
+// normal range; the accuracy budget of those terms is ~1e-7 absolute.
+__device__ __forceinline__ float fast_sqrt(float x)
+{
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 // First pass of the window test, in plain FP32: false only when t - t0 - nP
 // is certainly outside [win_lo, win_hi].  One FMA does the reduction with
 // the same epoch n as reduce_time; against the double-float result it drops
@@ -84,6 +93,10 @@ __device__ __forceinline__ bool maybe_in_window(float th, const GeomRec &r)
 //     keeps relative accuracy there; z = sqrt(U^2 + V^2 cos^2 i).
 //   Behind the star (cos phi <= 0, or V <= 0) returns PT_ZBEHIND.
 // *bad is set when Newton did not converge within max_iter steps.
+// FAST takes the Newton quotient with __fdividef (its denominator
+// 1 - e cos E lies in [1 - e, 1 + e]) and the final root as x * rsqrtf(x):
+// about one ulp more in z, for the Mandel-Agol kernels.
+template <bool FAST = false>
 __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_iter, bool *bad)
 {
     if (r.ecc == 0.0f) {
@@ -91,7 +104,7 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
         sincosf(r.nang * dt, &s, &c);
         if (c <= 0.0f) return PT_ZBEHIND;
         float ci = r.cosi * c;
-        return r.a * sqrtf(fmaf(s, s, ci * ci));
+        return r.a * (FAST ? fast_sqrt(fmaf(s, s, ci * ci)) : sqrtf(fmaf(s, s, ci * ci)));
     }
     float dM = r.nang * dt;
     float dE = dM / (1.0f - r.ecE);
@@ -102,7 +115,7 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
         float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
         float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
         float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
-        float step = F / Fp;
+        float step = FAST ? __fdividef(F, Fp) : F / Fp;
         dE -= step;
         if (fabsf(step) <= 4e-7f * fabsf(dE) + 1e-12f) {
             conv = true;
@@ -118,17 +131,9 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
     float V = r.Vtr + (r.Vs * dC + r.Vc * dS);
     if (V <= 0.0f) return PT_ZBEHIND;
     float Vi = V * r.cosi;
-    return sqrtf(fmaf(U, U, Vi * Vi));
+    return FAST ? fast_sqrt(fmaf(U, U, Vi * Vi)) : sqrtf(fmaf(U, U, Vi * Vi));
 }
 
-// Square root through the hardware reciprocal square root (about one ulp
-// off the correctly rounded value; exact zero at 0).  The Mandel-Agol terms
-// use it, and __fdividef, where their arguments are bounded well inside the
-// normal range; the accuracy budget of those terms is ~1e-7 absolute.
-__device__ __forceinline__ float fast_sqrt(float x)
-{
-    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
-}
 
 // ---------------------------------------------------------------------------
 // Bulirsch's general complete elliptic integral (Bulirsch 1969, Numer. Math.

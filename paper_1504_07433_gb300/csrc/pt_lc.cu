@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
             const GeomRec &r = srec[vl];
             float dts = sdt[vl][ti] + ss_offset(A.t_exp, s, nss);
             bool bad = false;
-            float z = pt::orbit_z(r, dts, A.max_iter, &bad);
+            float z = pt::orbit_z<true>(r, dts, A.max_iter, &bad);
             if (bad) atomicAdd(&sbad, 1);
             if constexpr (INTERP)
                 ma_interp(A.mtab, A.mn_k, A.mn_z, A.mk_lo, A.mk_hi, A.minv_dk, A.minv_dz, r.k, z, &le, &ld, &ed);
@@ -942,7 +942,7 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
 #pragma unroll 1
             for (int s = 0; s < nss; ++s) {
                 bool bad = false;
-                float z = pt::orbit_z(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad);
+                float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad);
                 if (bad) ++nbad;
                 float a0, a1, a2;
                 pt::ma_terms(srec.k, z, &a0, &a1, &a2);
