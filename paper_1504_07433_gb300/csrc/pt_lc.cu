@@ -366,6 +366,93 @@ struct GimArgs {
     int *n_bad;
 };
 
+// Double-float arithmetic for the table recursion: a value is the unevaluated
+// sum h + l of two floats (about 48 significant bits).  Sums and products
+// carry their rounding errors exactly (Knuth's two-sum; the FMA form of
+// Dekker's product).  GB300's FP64 rate is a small fraction of its FP32
+// rate, so a chain of FP64 operations would dominate the table work.
+struct DF {
+    float h, l;
+};
+
+__device__ __forceinline__ DF df_of(double v)
+{
+    float h = (float)v;
+    return DF{h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ DF df_norm(float s, float e)   // |s| >= |e|
+{
+    float h = s + e;
+    return DF{h, e - (h - s)};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    float s = a.h + b.h;
+    float bb = s - a.h;
+    float e = (a.h - (s - bb)) + (b.h - bb);
+    return df_norm(s, e + (a.l + b.l));
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    return df_norm(p, e);
+}
+
+// Gimenez per-geometry table for Clenshaw's summation: entry (n, j) packs the
+// z-recursion coefficients r1_j, r2_j, r3_{j+1} of G_j(nu+2, 1; x) with
+// T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2, the z-independent factor of
+// Sec. 2.1.4 (recursion in double-float arithmetic, stored FP32).
+// A table CTA covers one order n and TT geometries; row n of the plan's
+// coefficients is staged in shared memory as double-float pairs.  The
+// recursion is a chain of n_j dependent steps per thread, so the table CTAs
+// run inside the window kernel's launch, in the shadow of its wide grid.
+struct TableJob {
+    const GeomRec *rec;
+    int n_geom, NP1, n_j;
+    const double *A, *recb;   // the plan's A_{n,j} and recursion of G_j(nu+2, nu+1; x), FP64
+    const float4 *coef;       // the plan's recursion of G_j(nu+2, 1; x), FP32
+    float4 *tab;              // [n_geom][NP1][n_j]
+    int n_blocks;             // table CTAs (0: none)
+};
+
+__device__ __forceinline__ void table_cta(const TableJob &J, int n, int gb)
+{
+    extern __shared__ __align__(16) unsigned char tsm[];
+    const int n_j = J.n_j;
+    float4 *scf = reinterpret_cast<float4 *>(tsm);   // [n_j]
+    DF *sA = reinterpret_cast<DF *>(scf + n_j);      // [n_j]
+    DF *srb = sA + n_j;                              // [n_j][3]
+    for (int i = threadIdx.x; i < n_j; i += blockDim.x) {
+        scf[i] = J.coef[(size_t)n * n_j + i];
+        sA[i] = df_of(J.A[(size_t)n * n_j + i]);
+    }
+    for (int i = threadIdx.x; i < 3 * n_j; i += blockDim.x) srb[i] = df_of(J.recb[(size_t)n * n_j * 3 + i]);
+    __syncthreads();
+    const int g = gb * blockDim.x + threadIdx.x;
+    if (g >= J.n_geom) return;
+    const double k = J.rec[g].k;
+    const DF x = df_of(1.0 - k / (1.0 + k));
+    float4 *out = J.tab + ((size_t)g * J.NP1 + n) * n_j;
+    DF gp = DF{0.0f, 0.0f}, gc = DF{1.0f, 0.0f};
+    for (int j = 0; j < n_j; ++j) {
+        float4 c = scf[j];
+        float r3n = (j + 1 < n_j) ? scf[j + 1].z : 0.0f;
+        DF t = df_mul(df_mul(sA[j], gc), gc);
+        out[j] = make_float4(c.x, c.y, r3n, t.h + t.l);
+        DF al = df_add(srb[3 * j], df_mul(srb[3 * j + 1], x));
+        DF gn = df_add(df_mul(al, gc), df_mul(srb[3 * j + 2], gp));
+        gp = gc;
+        gc = gn;
+    }
+}
+
+size_t gim_table_smem(int n_j) { return (size_t)n_j * (sizeof(float4) + 4 * sizeof(DF)); }
+
 // One CTA covers TT times x GW_VT geometries.  The first pass of the window
 // test (as pt::maybe_in_window, but with its margin bounded once per tile and
 // geometry from the tile's largest |t_h|) costs a subtraction, a product, a
@@ -375,7 +462,7 @@ struct GimArgs {
 // per geometry, one global atomic per geometry reserves the CTA's stretch of
 // its list, and the same ballots place every pair (warp order, then lane
 // order) inside that stretch.  Every other pair gets flux 1.
-__global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A)
+__device__ __forceinline__ void window_cta(const GimArgs &A, int bx, int by)
 {
     constexpr int NW = TT / 32;
     __shared__ GeomRec srec[GW_VT];
@@ -385,13 +472,13 @@ __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A)
     __shared__ int sbase[GW_VT];
     __shared__ float swmax[NW];
     const int tl = threadIdx.x, lane = tl & 31, warp = tl >> 5;
-    const int g0 = blockIdx.y * GW_VT;
+    const int g0 = by * GW_VT;
     const int ng = min(GW_VT, A.n_geom - g0);
     for (int i = tl; i < ng * 6; i += TT) {
         int vl = i / 6, c = i % 6;
         reinterpret_cast<float4 *>(&srec[vl])[c] = reinterpret_cast<const float4 *>(&A.rec[g0 + vl])[c];
     }
-    const int t = blockIdx.x * TT + tl;
+    const int t = bx * TT + tl;
     const bool tv = t < A.n_t;
     const float2 ts = tv ? A.tsplit[t] : make_float2(0.0f, 0.0f);
     // the tile's largest |t_h| (non-negative floats order like their bits)
@@ -464,6 +551,19 @@ __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A)
                     if (!((bits >> vl) & 1u)) *fp = 1.0f;
         }
     }
+}
+
+// One launch: J.n_blocks table CTAs first (they start first and run in the
+// shadow of the window CTAs), then n_tiles x ceil(n_geom / GW_VT) window CTAs.
+__global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A, TableJob J, int n_tiles)
+{
+    int id = blockIdx.x;
+    if (id < J.n_blocks) {
+        table_cta(J, id % J.NP1, id / J.NP1);
+        return;
+    }
+    id -= J.n_blocks;
+    window_cta(A, id % n_tiles, id / n_tiles);
 }
 
 // pref[g] = sum over g' < g of ceil(cnt[g'] / ppi); pref[n_geom] = total.
@@ -967,84 +1067,6 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
     if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
 }
 
-// Double-float arithmetic for the table recursion: a value is the unevaluated
-// sum h + l of two floats (about 48 significant bits).  Sums and products
-// carry their rounding errors exactly (Knuth's two-sum; the FMA form of
-// Dekker's product).  GB300's FP64 rate is a small fraction of its FP32
-// rate, so a chain of FP64 operations would dominate this kernel.
-struct DF {
-    float h, l;
-};
-
-__device__ __forceinline__ DF df_of(double v)
-{
-    float h = (float)v;
-    return DF{h, (float)(v - (double)h)};
-}
-
-__device__ __forceinline__ DF df_norm(float s, float e)   // |s| >= |e|
-{
-    float h = s + e;
-    return DF{h, e - (h - s)};
-}
-
-__device__ __forceinline__ DF df_add(DF a, DF b)
-{
-    float s = a.h + b.h;
-    float bb = s - a.h;
-    float e = (a.h - (s - bb)) + (b.h - bb);
-    return df_norm(s, e + (a.l + b.l));
-}
-
-__device__ __forceinline__ DF df_mul(DF a, DF b)
-{
-    float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
-    return df_norm(p, e);
-}
-
-// Gimenez per-geometry table for Clenshaw's summation: entry (n, j) packs the
-// z-recursion coefficients r1_j, r2_j, r3_{j+1} of G_j(nu+2, 1; x) with
-// T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2, the z-independent factor of
-// Sec. 2.1.4 (recursion in double-float arithmetic, stored FP32).
-// One CTA per (n, 32 geometries): row n of the plan's coefficients is staged
-// in shared memory as double-float pairs.
-__global__ void __launch_bounds__(32) gim_table_kernel(const GeomRec *rec, int n_geom, int n_j, const double *A,
-                                                      const double *recb, const float4 *coef, float4 *tab)
-{
-    extern __shared__ __align__(16) unsigned char tsm[];
-    float4 *scf = reinterpret_cast<float4 *>(tsm);   // [n_j]
-    DF *sA = reinterpret_cast<DF *>(scf + n_j);      // [n_j]
-    DF *srb = sA + n_j;                              // [n_j][3]
-    const int n = blockIdx.y;
-    const int NP1 = gridDim.y;
-    for (int i = threadIdx.x; i < n_j; i += blockDim.x) {
-        scf[i] = coef[(size_t)n * n_j + i];
-        sA[i] = df_of(A[(size_t)n * n_j + i]);
-    }
-    for (int i = threadIdx.x; i < 3 * n_j; i += blockDim.x) srb[i] = df_of(recb[(size_t)n * n_j * 3 + i]);
-    __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_geom) return;
-    const double k = rec[g].k;
-    const DF x = df_of(1.0 - k / (1.0 + k));
-    float4 *out = tab + ((size_t)g * NP1 + n) * n_j;
-    DF gp = DF{0.0f, 0.0f}, gc = DF{1.0f, 0.0f};
-    for (int j = 0; j < n_j; ++j) {
-        float4 c = scf[j];
-        float r3n = (j + 1 < n_j) ? scf[j + 1].z : 0.0f;
-        DF t = df_mul(df_mul(sA[j], gc), gc);
-        out[j] = make_float4(c.x, c.y, r3n, t.h + t.l);
-        DF al = df_add(srb[3 * j], df_mul(srb[3 * j + 1], x));
-        DF gn = df_add(df_mul(al, gc), df_mul(srb[3 * j + 2], gp));
-        gp = gc;
-        gc = gn;
-    }
-}
-
-size_t gim_table_smem(int n_j) { return (size_t)n_j * (sizeof(float4) + 4 * sizeof(DF)); }
-
 __global__ void ssr_reduce_kernel(const float *part, int rows, int n_tiles, float *ssr)
 {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1542,7 +1564,11 @@ static int ma_quad_list(const double *t, int n_t, const pt_orbit *orb, const flo
     A.list = (int *)(wb + L.list);
     A.ppi = MA_PPI;
     A.n_bad = n_bad;
-    gim_window_kernel<<<dim3(n_tiles, gy), TT, 0, s>>>(A);
+    TableJob J;
+    memset(&J, 0, sizeof(J));
+    const size_t n_cta = (size_t)n_tiles * gy;
+    if (n_cta > 0x7fffffffULL) return PT_ERR_ARG;
+    gim_window_kernel<<<(unsigned)n_cta, TT, 0, s>>>(A, J, n_tiles);
     st = check_launch("gim_window_kernel");
     if (st) return st;
     gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, MA_PPI, A.pref, A.ctr);
@@ -1816,16 +1842,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     int *cnt = (int *)(wb + L.cnt);
     st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, cnt, s);
     if (st) return st;
-    gim_table_kernel<<<dim3((n_geom + 31) / 32, NP1), 32, gim_table_smem(plan->n_j), s>>>(
-        rec, n_geom, plan->n_j, plan->d_A, plan->d_recb, plan->d_coef, T);
-    st = check_launch("gim_table_kernel");
-    if (st) return st;
     float *atab = (float *)(wb + L.atab);
-    if (zi) {
-        gim_zi_table_kernel<<<n_geom, 128, 0, s>>>(rec, T, NP1, plan->n_j, n_in, n_edge, atab);
-        st = check_launch("gim_zi_table_kernel");
-        if (st) return st;
-    }
     GimArgs A;
     memset(&A, 0, sizeof(A));
     A.tsplit = tsplit;
@@ -1847,9 +1864,36 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     A.list = (int *)(wb + L.list);
     A.ppi = (n_ss >= 20) ? GS_THREADS / 2 : GS_THREADS;
     A.n_bad = n_bad;
-    gim_window_kernel<<<dim3(n_tiles, gy), TT, 0, s>>>(A);
+    TableJob J;
+    J.rec = rec;
+    J.n_geom = n_geom;
+    J.NP1 = NP1;
+    J.n_j = plan->n_j;
+    J.A = plan->d_A;
+    J.recb = plan->d_recb;
+    J.coef = plan->d_coef;
+    J.tab = T;
+    J.n_blocks = NP1 * ((n_geom + TT - 1) / TT);
+    const size_t tsm = gim_table_smem(plan->n_j);
+    if (tsm > 48 * 1024) {
+        static thread_local size_t tsm_configured = 0;
+        if (tsm > tsm_configured) {
+            cudaError_t e = cudaFuncSetAttribute(gim_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)tsm);
+            if (e != cudaSuccess) return set_cuda_error(e, "gim_window_kernel smem attribute");
+            tsm_configured = tsm;
+        }
+    }
+    const size_t n_cta = (size_t)J.n_blocks + (size_t)n_tiles * gy;
+    if (n_cta > 0x7fffffffULL) return PT_ERR_ARG;
+    gim_window_kernel<<<(unsigned)n_cta, TT, tsm, s>>>(A, J, n_tiles);
     st = check_launch("gim_window_kernel");
     if (st) return st;
+    if (zi) {
+        gim_zi_table_kernel<<<n_geom, 128, 0, s>>>(rec, T, NP1, plan->n_j, n_in, n_edge, atab);
+        st = check_launch("gim_zi_table_kernel");
+        if (st) return st;
+    }
     gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, A.ppi, A.pref, A.ctr);
     st = check_launch("gim_scan_kernel");
     if (st) return st;
