@@ -825,6 +825,281 @@ __global__ void __launch_bounds__(GS_THREADS, GS_MIN_CTAS) gim_series_kernel(Gim
 size_t gim_series_smem(int N, int n_j) { return (size_t)(N + 1) * n_j * sizeof(float4); }
 
 // ---------------------------------------------------------------------------
+// Chebyshev form of the series.  For one geometry and order n,
+//   S_n(x) = sum_{j < n_j} T_{n,j} G_j(nu+2, 1; x)
+// is a polynomial of degree n_j - 1 in x, so it equals its interpolant at the
+// n_j Chebyshev nodes x_i = (1 + cos(pi (i + 1/2) / n_j)) / 2:
+//   S_n(x) = sum_{m < n_j} d_{n,m} T_m(2x - 1),
+//   d_{n,m} = (2 - [m = 0]) / n_j  sum_i cos(pi m (i + 1/2) / n_j) S_n(x_i)
+// (the discrete cosine transform of the node values; exact for a polynomial
+// of that degree).  The Chebyshev basis does not depend on n, so one
+// recurrence T_{m+1} = 2y T_m - T_{m-1} per supersample serves all N + 1
+// orders, and the orders accumulate two at a time in two-lane FMAs: about
+// (N + 3) FMAs per term instead of 3 (N + 1).
+// gim_cheb_coef_kernel: one CTA per geometry; node values by the same
+// Clenshaw summation as the series kernel (FP32), then the transform with
+// compensated sums (each product and its FMA-exact error added by a two-sum).
+// ---------------------------------------------------------------------------
+// One CTA per (geometry, pair of orders), so that enough warps hide the
+// dependent chains: the node values of the two orders, then their two
+// coefficient rows (one thread per m, cosine table through shared memory).
+// Orders past N (padding of the coefficient rows) get zeros.
+constexpr int CC_CI = 16;   // cosine-table rows per shared-memory chunk
+constexpr int CC_MR = 4;    // coefficient rows per thread: n_j <= CC_MR * 128
+
+__global__ void __launch_bounds__(128) gim_cheb_coef_kernel(const float4 *gtab, int NP1, int n_j, int DS,
+                                                           const float *cx, const float *ccos, float *dtab)
+{
+    extern __shared__ __align__(16) unsigned char csm[];
+    const int g = blockIdx.x;
+    const int n0 = 2 * blockIdx.y;
+    const int no = min(2, max(0, NP1 - n0));   // orders of this CTA that exist
+    float4 *stab = reinterpret_cast<float4 *>(csm);     // [2][n_j]
+    float *sS = reinterpret_cast<float *>(stab + 2 * n_j);   // [n_j][2]
+    float *scos = sS + 2 * n_j;                          // [CC_CI][n_j]
+    if (no > 0) {
+        const float4 *src = gtab + ((size_t)g * NP1 + n0) * n_j;
+        for (int i = threadIdx.x; i < no * n_j; i += blockDim.x) stab[i] = src[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_j; i += blockDim.x) {
+        const float x = cx[i];
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            float c1 = 0.0f;
+            if (o < no) {
+                const float4 *tn = stab + o * n_j;
+                float c2 = 0.0f;
+#pragma unroll 4
+                for (int j = n_j - 1; j >= 0; --j) {
+                    float4 c = tn[j];
+                    float bj = fmaf(fmaf(c.y, x, c.x), c1, fmaf(c.z, c2, c.w));
+                    c2 = c1;
+                    c1 = bj;
+                }
+            }
+            sS[2 * i + o] = c1;
+        }
+    }
+    float sum[CC_MR][2], err[CC_MR][2];
+#pragma unroll
+    for (int r = 0; r < CC_MR; ++r) sum[r][0] = sum[r][1] = err[r][0] = err[r][1] = 0.0f;
+    if (no > 0) {
+        for (int i0 = 0; i0 < n_j; i0 += CC_CI) {
+            const int ci = min(CC_CI, n_j - i0);
+            __syncthreads();
+            if ((n_j & 3) == 0) {   // 128-bit copies, issued together
+                const float4 *cs4 = reinterpret_cast<const float4 *>(ccos + (size_t)i0 * n_j);
+                float4 *sc4 = reinterpret_cast<float4 *>(scos);
+                const int ne = ci * n_j / 4;
+#pragma unroll 4
+                for (int e = threadIdx.x; e < ne; e += blockDim.x) sc4[e] = cs4[e];
+            } else {
+#pragma unroll 4
+                for (int e = threadIdx.x; e < ci * n_j; e += blockDim.x) scos[e] = ccos[(size_t)i0 * n_j + e];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < CC_MR; ++r) {
+                const int m = threadIdx.x + r * blockDim.x;
+                if (m >= n_j) break;
+                for (int ii = 0; ii < ci; ++ii) {
+                    const float a = scos[ii * n_j + m];
+                    const float2 v2 = reinterpret_cast<const float2 *>(sS)[i0 + ii];
+#pragma unroll
+                    for (int o = 0; o < 2; ++o) {
+                        const float v = o ? v2.y : v2.x;
+                        const float pr = a * v;
+                        const float pe = fmaf(a, v, -pr);
+                        const float ts = sum[r][o] + pr;
+                        const float bv = ts - sum[r][o];
+                        err[r][o] += ((sum[r][o] - (ts - bv)) + (pr - bv)) + pe;
+                        sum[r][o] = ts;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < CC_MR; ++r) {
+        const int m = threadIdx.x + r * blockDim.x;
+        if (m >= n_j) break;
+        float2 o2 = make_float2(no > 0 ? sum[r][0] + err[r][0] : 0.0f, no > 1 ? sum[r][1] + err[r][1] : 0.0f);
+        reinterpret_cast<float2 *>(dtab + ((size_t)g * n_j + m) * DS)[blockIdx.y] = o2;
+    }
+}
+
+size_t gim_cheb_coef_smem(int n_j)
+{
+    // two orders' table rows and node values, and a chunk of the cosine table
+    return (size_t)n_j * (2 * sizeof(float4) + 2 * sizeof(float) + CC_CI * sizeof(float));
+}
+
+// Evaluation over the pair lists: persistent CTAs take items of GS_THREADS
+// listed pairs and stage the geometry's coefficients d[m][n] (n padded to an
+// even count) once per item; each thread evaluates its pair's in-transit
+// supersamples one by one (x = c^2, q = sqrt(1 - x), y = 2x - 1), with the
+// Chebyshev recurrence in one lane pair and NPAIR two-lane accumulators for
+// orders (2p, 2p+1), whose coefficient pairs load from shared memory as
+// 64-bit operands.  alpha_n = b^2 q^(n+4) S_n is summed over the supersamples
+// in order, then the passband combination of Sec. 2.1.3.
+template <int NPAIR>
+__global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const float *dtab)
+{
+    constexpr int DS = (2 * NPAIR + 3) & ~3;   // floats per coefficient row
+    constexpr int SG = 2;                       // supersamples per group (share the coefficient loads)
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float *sd = reinterpret_cast<float *>(dsm);   // [n_j][DS]
+    __shared__ GeomRec srec;
+    __shared__ int sitem, sgeom, sbad;
+    const int NP1 = A.N + 1;
+    const int nj = A.n_j;
+    const int nss = A.n_ss;
+    const int tid = threadIdx.x;
+    const int total = A.pref[A.n_geom];
+    const float inv_nss = 1.0f / (float)nss;
+    int nbad = 0;
+    int staged = -1;
+    if (tid == 0) sbad = 0;
+#pragma unroll 1
+    for (;;) {
+        if (tid == 0) {
+            int it = atomicAdd(A.ctr, 1);
+            int g = -1;
+            if (it < total) {   // the largest g with pref[g] <= it
+                int lo = 0, hi = A.n_geom - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (A.pref[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                g = lo;
+            }
+            sitem = it;
+            sgeom = g;
+        }
+        __syncthreads();
+        const int it = sitem;
+        const int g = sgeom;
+        if (it >= total) break;   // uniform over the CTA
+        if (g != staged) {
+            const float4 *src = reinterpret_cast<const float4 *>(dtab + (size_t)g * nj * DS);
+            float4 *dst = reinterpret_cast<float4 *>(sd);
+            for (int i = tid; i < nj * DS / 4; i += GS_THREADS) dst[i] = src[i];
+            if (tid < 6) reinterpret_cast<float4 *>(&srec)[tid] = reinterpret_cast<const float4 *>(&A.rec[g])[tid];
+            staged = g;
+        }
+        __syncthreads();
+        const int i = (it - A.pref[g]) * GS_THREADS + tid;
+        if (i < A.cnt[g]) {
+            const int t = A.list[(size_t)g * A.n_t + i];
+            float2 ts = A.tsplit[t];
+            const float dt = pt::reduce_time(ts.x, ts.y, srec);
+            const float kk = srec.k;
+            const float bk = kk / (1.0f + kk);
+            const float b2 = bk * bk;
+            unsigned long long aa[NPAIR];   // alpha sums over the supersamples, orders (2p, 2p+1)
+#pragma unroll
+            for (int p = 0; p < NPAIR; ++p) aa[p] = 0ull;
+#pragma unroll 1
+            for (int s0 = 0; s0 < nss; s0 += SG) {
+                float y[SG], q[SG];
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < SG; ++u) {
+                    y[u] = 0.0f;   // out of transit: q = 0 gives the supersample weight 0
+                    q[u] = 0.0f;
+                    if (s0 + u < nss) {
+                        bool bad = false;
+                        float z = pt::orbit_z(srec, dt + ss_offset(A.t_exp, s0 + u, nss), A.max_iter, &bad);
+                        if (bad) ++nbad;
+                        if (z < 1.0f + kk) {
+                            const float c = z / (1.0f + kk);
+                            const float x = c * c;
+                            q[u] = sqrtf((1.0f - c) * (1.0f + c));
+                            y[u] = fmaf(2.0f, x, -1.0f);
+                        }
+                    }
+                    any |= q[u] > 0.0f;
+                }
+                if (!any) continue;
+                unsigned long long acc[SG][NPAIR];
+                float t0[SG], t1[SG];
+                {
+                    const unsigned long long *d0 = reinterpret_cast<const unsigned long long *>(sd);
+                    const unsigned long long *d1 = reinterpret_cast<const unsigned long long *>(sd + DS);
+#pragma unroll
+                    for (int u = 0; u < SG; ++u) {
+                        const unsigned long long ty = f2_pack(y[u], y[u]);
+#pragma unroll
+                        for (int p = 0; p < NPAIR; ++p) acc[u][p] = f2_fma(d1[p], ty, d0[p]);
+                        t0[u] = 1.0f;
+                        t1[u] = y[u];
+                    }
+                }
+#pragma unroll 2
+                for (int m = 2; m < nj; ++m) {
+                    unsigned long long dm[NPAIR];
+                    const ulonglong2 *row = reinterpret_cast<const ulonglong2 *>(sd + m * DS);
+#pragma unroll
+                    for (int p = 0; p + 1 < NPAIR; p += 2) {
+                        ulonglong2 v = row[p / 2];
+                        dm[p] = v.x;
+                        dm[p + 1] = v.y;
+                    }
+                    if (NPAIR & 1) dm[NPAIR - 1] = reinterpret_cast<const unsigned long long *>(row)[NPAIR - 1];
+#pragma unroll
+                    for (int u = 0; u < SG; ++u) {
+                        const float t2 = fmaf(y[u] + y[u], t1[u], -t0[u]);
+                        const unsigned long long tt = f2_pack(t2, t2);
+#pragma unroll
+                        for (int p = 0; p < NPAIR; ++p) acc[u][p] = f2_fma(dm[p], tt, acc[u][p]);
+                        t0[u] = t1[u];
+                        t1[u] = t2;
+                    }
+                }
+                // alpha_n = b^2 q^(n+4) S_n, summed over the supersamples in order
+#pragma unroll
+                for (int u = 0; u < SG; ++u) {
+                    const float qq = q[u] * q[u];
+                    float w = b2 * qq * qq;
+#pragma unroll
+                    for (int p = 0; p < NPAIR; ++p) {
+                        aa[p] = f2_fma(acc[u][p], f2_pack(w, w * q[u]), aa[p]);
+                        w *= qq;
+                    }
+                }
+            }
+            float al[2 * NPAIR];
+#pragma unroll
+            for (int p = 0; p < NPAIR; ++p) f2_split(aa[p], al[2 * p], al[2 * p + 1]);
+#pragma unroll 1
+            for (int bb = 0; bb < A.n_bpg; ++bb) {
+                size_t row = (size_t)g * A.n_bpg + bb;
+                const float *u = A.ld + row * A.N;
+                // C_0 = (1 - sum u)/D, C_n = u_n/D, D = 1 - sum n u_n/(n+2)   (Sec. 2.1.3)
+                float su = 0.0f, sdn = 0.0f;
+                for (int n = 1; n <= A.N; ++n) {
+                    float un = u[n - 1];
+                    su += un;
+                    sdn += (float)n * un / (float)(n + 2);
+                }
+                float acc_f = (1.0f - su) * al[0];
+#pragma unroll
+                for (int n = 1; n < 2 * NPAIR; ++n)
+                    if (n < NP1) acc_f = fmaf(u[n - 1], al[n], acc_f);
+                A.flux[row * A.n_t + t] = 1.0f - acc_f / (1.0f - sdn) * inv_nss;
+            }
+        }
+    }
+    if (nbad) atomicAdd(&sbad, nbad);
+    __syncthreads();
+    if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
+}
+
+size_t gim_cheb_smem(int n_j, int NPAIR) { return (size_t)n_j * ((2 * NPAIR + 3) & ~3) * sizeof(float); }
+
+// ---------------------------------------------------------------------------
 // Gimenez model interpolated in z (Sec. 3.3).  gim_zi_table_kernel evaluates
 // alpha_0..alpha_N of every geometry on its z nodes (n_in over [0, zb],
 // zb = max(1 - k, 0), then n_edge over (zb, 1 + k]) with the same Clenshaw
@@ -1266,7 +1541,7 @@ int check_orbit(const pt_orbit *orb, bool need_ecc)
 // work-item counter), work-item prefix, pair lists and a flux scratch used
 // when only residuals are asked for.
 struct WorkLayout {
-    size_t rec, tsplit, T, part, cnt, pref, list, fscr, atab, total;
+    size_t rec, tsplit, T, part, cnt, pref, list, fscr, atab, dtab, total;
 };
 
 // n_zi > 0 adds the z tables of the interpolated Gimenez model.
@@ -1280,7 +1555,7 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
     off += align256((size_t)n_geom * sizeof(GeomRec));
     L.tsplit = off;
     off += align256((size_t)n_t * sizeof(float2));
-    L.T = L.part = L.cnt = L.pref = L.list = L.fscr = L.atab = off;
+    L.T = L.part = L.cnt = L.pref = L.list = L.fscr = L.atab = L.dtab = off;
     if (NP1 == 0) {
         L.part = off;
         off += align256((size_t)n_v * n_b * n_tiles * sizeof(float));
@@ -1297,6 +1572,8 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
         off += align256((size_t)n_v * n_b * n_t * sizeof(float));
         L.atab = off;
         off += align256((size_t)n_geom * n_zi * NP1 * sizeof(float));
+        L.dtab = off;   // Chebyshev coefficients, orders padded to an even count
+        off += align256((size_t)n_geom * n_j * (((NP1 + 1) & ~1) + 3 & ~3) * sizeof(float));
     }
     L.total = off;
     return L;
@@ -1325,6 +1602,8 @@ struct pt_gim_plan_s {
     float4 *d_coef;   // [N+1][n_j]: recursion of G_j(nu+2, 1; x), FP32
     double *d_A;      // [N+1][n_j]: A_{n,j}, FP64
     double *d_recb;   // [N+1][n_j][3]: recursion of G_j(nu+2, nu+1; x), FP64
+    float *d_cx;      // [n_j]: Chebyshev nodes in x, (1 + cos(pi (i + 1/2) / n_j)) / 2
+    float *d_ccos;    // [n_j (i)][n_j (m)]: (2 / n_j) cos(pi m (i + 1/2) / n_j), column m = 0 halved
 };
 
 namespace {
@@ -1404,6 +1683,68 @@ int launch_zi(const GimArgs &A, const float *atab, int n_in, int n_edge, size_t 
     if (grid < 1) grid = 1;
     gim_zi_kernel<<<(unsigned)grid, GS_THREADS, smem, s>>>(A, atab, n_in, n_edge);
     return check_launch("gim_zi_kernel");
+}
+
+// The series evaluated in its Chebyshev form (gim_cheb_kernel) instead of
+// gim_series_kernel's per-order Clenshaw summation.
+constexpr bool G_CHEB = true;
+
+template <int NPAIR>
+int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab,
+                  size_t max_items, cudaStream_t s)
+{
+    // coefficients: one CTA per (geometry, pair of orders), every row of
+    // DS floats written (orders past N as zeros)
+    constexpr int DS = (2 * NPAIR + 3) & ~3;
+    const size_t csm = gim_cheb_coef_smem(A.n_j);
+    static thread_local size_t csm_configured = 0;
+    if (csm > 48 * 1024 && csm > csm_configured) {
+        cudaError_t e = cudaFuncSetAttribute(gim_cheb_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)csm);
+        if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_coef_kernel smem attribute");
+        csm_configured = csm;
+    }
+    gim_cheb_coef_kernel<<<dim3(A.n_geom, DS / 2), 128, csm, s>>>(T, A.N + 1, A.n_j, DS, cx, ccos, dtab);
+    int st = check_launch("gim_cheb_coef_kernel");
+    if (st) return st;
+    // evaluation: persistent
+    const size_t smem = gim_cheb_smem(A.n_j, NPAIR);
+    static thread_local size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(gim_cheb_kernel<NPAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_kernel smem attribute");
+        configured = smem;
+    }
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gim_cheb_kernel<NPAIR>, GS_THREADS, smem);
+    if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_kernel occupancy");
+    if (per_sm < 1) return pt_internal::set_error(PT_ERR_ARG, "gim_cheb_kernel", "does not fit on an SM");
+    size_t grid = (size_t)n_sm * per_sm;
+    if (grid > max_items) grid = max_items;
+    if (grid < 1) grid = 1;
+    gim_cheb_kernel<NPAIR><<<(unsigned)grid, GS_THREADS, smem, s>>>(A, dtab);
+    return check_launch("gim_cheb_kernel");
+}
+
+// Chebyshev path: coefficient and evaluation kernels, for NPAIR = ceil((N + 1) / 2).
+int launch_cheb(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab, size_t max_items,
+                cudaStream_t s)
+{
+    switch ((A.N + 2) / 2) {
+    case 1: return launch_cheb_t<1>(A, T, cx, ccos, dtab, max_items, s);
+    case 2: return launch_cheb_t<2>(A, T, cx, ccos, dtab, max_items, s);
+    case 3: return launch_cheb_t<3>(A, T, cx, ccos, dtab, max_items, s);
+    case 4: return launch_cheb_t<4>(A, T, cx, ccos, dtab, max_items, s);
+    case 5: return launch_cheb_t<5>(A, T, cx, ccos, dtab, max_items, s);
+    case 6: return launch_cheb_t<6>(A, T, cx, ccos, dtab, max_items, s);
+    case 7: return launch_cheb_t<7>(A, T, cx, ccos, dtab, max_items, s);
+    case 8: return launch_cheb_t<8>(A, T, cx, ccos, dtab, max_items, s);
+    default: return launch_cheb_t<9>(A, T, cx, ccos, dtab, max_items, s);
+    }
 }
 
 }  // namespace
@@ -1753,25 +2094,44 @@ int pt_gim_plan_create(int N, int n_j, pt_gim_plan *out)
             for (int c = 0; c < 3; ++c) hrb[((size_t)n * n_j + j) * 3 + c] = r[c];
         }
     }
+    // Chebyshev nodes and the discrete cosine transform of the series-
+    // evaluation change of basis (FP64 here, stored FP32)
+    float *hcx = new float[n_j];
+    float *hcc = new float[(size_t)n_j * n_j];
+    for (int i = 0; i < n_j; ++i) hcx[i] = (float)(0.5 * (1.0 + cos(PI_D * (i + 0.5) / n_j)));
+    for (int m = 0; m < n_j; ++m)
+        for (int i = 0; i < n_j; ++i)
+            hcc[(size_t)i * n_j + m] = (float)((m == 0 ? 1.0 : 2.0) / n_j * cos(PI_D * m * (i + 0.5) / n_j));
     pt_gim_plan p = new pt_gim_plan_s;
     p->N = N;
     p->n_j = n_j;
     p->d_coef = nullptr;
     p->d_A = nullptr;
     p->d_recb = nullptr;
+    p->d_cx = nullptr;
+    p->d_ccos = nullptr;
     cudaError_t e = cudaMalloc(&p->d_coef, cnt * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_A, cnt * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_recb, cnt * 3 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_coef, hcoef, cnt * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_A, hA, cnt * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_recb, hrb, cnt * 3 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_cx, n_j * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_ccos, (size_t)n_j * n_j * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_cx, hcx, n_j * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_ccos, hcc, (size_t)n_j * n_j * sizeof(float), cudaMemcpyHostToDevice);
     delete[] hcoef;
     delete[] hA;
     delete[] hrb;
+    delete[] hcx;
+    delete[] hcc;
     if (e != cudaSuccess) {
         cudaFree(p->d_coef);
         cudaFree(p->d_A);
         cudaFree(p->d_recb);
+        cudaFree(p->d_cx);
+        cudaFree(p->d_ccos);
         delete p;
         return set_cuda_error(e, "pt_gim_plan_create");
     }
@@ -1785,6 +2145,8 @@ int pt_gim_plan_destroy(pt_gim_plan p)
     cudaFree(p->d_coef);
     cudaFree(p->d_A);
     cudaFree(p->d_recb);
+    cudaFree(p->d_cx);
+    cudaFree(p->d_ccos);
     delete p;
     return PT_OK;
 }
@@ -1862,7 +2224,10 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     A.pref = (int *)(wb + L.pref);
     A.ctr = cnt + n_geom;
     A.list = (int *)(wb + L.list);
-    A.ppi = (n_ss >= 20) ? GS_THREADS / 2 : GS_THREADS;
+    // items of GS_THREADS listed pairs; only the per-order series kernel
+    // splits a long supersample list over two threads per pair
+    const bool cheb = !zi && G_CHEB;
+    A.ppi = (!zi && !cheb && n_ss >= 20) ? GS_THREADS / 2 : GS_THREADS;
     A.n_bad = n_bad;
     TableJob J;
     J.rec = rec;
@@ -1894,6 +2259,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
         st = check_launch("gim_zi_table_kernel");
         if (st) return st;
     }
+    float *dtab = (float *)(wb + L.dtab);
     gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, A.ppi, A.pref, A.ctr);
     st = check_launch("gim_scan_kernel");
     if (st) return st;
@@ -1904,6 +2270,8 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     const size_t max_items = (size_t)n_geom * ((n_t + A.ppi - 1) / A.ppi);
     if (zi)
         st = launch_zi(A, atab, n_in, n_edge, smem, max_items, s);
+    else if (cheb)
+        st = launch_cheb(A, T, plan->d_cx, plan->d_ccos, dtab, (size_t)n_geom * ((n_t + GS_THREADS - 1) / GS_THREADS), s);
     else if (h == 1)
         st = launch_series<1>(A, smem, max_items, s);
     else if (h <= 2)
