@@ -328,22 +328,21 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 // series kernel accumulates, for n = 0..N,
 //   alpha_n = b^2 (1 - c^2)^{nu+1} sum_j T_{n,j} G_j(nu+2, 1; c^2),
 // with only summations and multiplications in the z-dependent part
-// (Sec. 2.1.4).  Three kernels:
-//   gim_window_kernel  every pair: window test; pairs in the window go to a
-//                      per-geometry list, the others get flux 1;
+// (Sec. 2.1.4).  Kernels:
+//   gim_window_kernel  the tables (leading CTAs); then every pair: window
+//                      test; pairs in the window go to a per-geometry list,
+//                      the others get flux 1;
 //   gim_scan_kernel    work items per geometry (ppi listed pairs each) and
 //                      their exclusive prefix;
-//   gim_series_kernel  persistent CTAs take work items from an atomic
-//                      counter, stage the geometry's table once per item and
-//                      give each pair one thread (two threads, each with
-//                      half of the supersamples, for long supersample lists).
+//   gim_cheb_coef_kernel / gim_cheb_kernel  the series in a Chebyshev basis
+//                      shared by the orders (below): coefficients per
+//                      geometry, then persistent CTAs that take work items
+//                      from an atomic counter and give each pair one thread.
 // Every pair's flux is computed by the same threads in the same order
 // whatever CTA takes its item, so the result is deterministic.
 // ---------------------------------------------------------------------------
 constexpr int GW_VT = 32;         // geometries per CTA of the window kernel (<= 32: one bit each)
-constexpr int GS_THREADS = 128;   // threads per CTA of the series kernel
-constexpr int GS_MIN_CTAS = 6;    // resident CTAs per SM the register budget is sized for
-constexpr int G_MAX_NP1 = 17;     // N <= 16
+constexpr int GS_THREADS = 128;   // threads per CTA of the evaluation kernels (one pair each)
 
 struct GimArgs {
     const float2 *tsplit;
@@ -611,7 +610,8 @@ __global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_ge
 
 // Two-lane FP32 arithmetic (sm_100 family): a 64-bit register holds two
 // floats and one fma.rn.f32x2 performs both lanes' FMAs, each rounded like
-// fmaf.  Two supersamples of a pair ride in the two lanes.
+// fmaf.  The Chebyshev evaluation keeps two orders of the series in the two
+// lanes.
 __device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
 {
     unsigned long long r;
@@ -632,197 +632,6 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
     return d;
 }
 
-// One thread's share of a pair: supersamples [s_lo, s_hi), SB at a time.
-// For each block the supersamples' z give x = c^2 and q = sqrt(1 - c^2)
-// (c = z / (1 + k)); then for every n Clenshaw's backward summation of
-// S = sum_j T_j G_j with G_{j+1} = (r1_j + r2_j x) G_j + r3_j G_{j-1},
-// G_0 = 1, G_{-1} = 0:
-//   b_j = T_j + (r1_j + r2_j x) b_{j+1} + r3_{j+1} b_{j+2},  S = b_0,
-// three FMAs per term and supersample, two supersamples per two-lane FMA
-// when SB is even; (1 - c^2)^{nu+1} = q^4 q^n with nu = (n+2)/2.  The
-// partial alpha_n go to salpha[n] (this thread's column).
-template <int SB>
-__device__ __forceinline__ void gim_pair(const float4 *stab, int NP1, int n_j, const GeomRec &r, float dt,
-                                         float t_exp, int nss, int s_lo, int s_hi, int max_iter,
-                                         float (*salpha)[GS_THREADS], int col, int *nbad)
-{
-    const float kk = r.k;
-    const float bk = kk / (1.0f + kk);
-    const float b2 = bk * bk;
-#pragma unroll 1
-    for (int s0 = s_lo; s0 < s_hi; s0 += SB) {
-        float x[SB], q[SB];
-        bool any = false;
-#pragma unroll
-        for (int u = 0; u < SB; ++u) {
-            int s = s0 + u;
-            x[u] = 0.0f;
-            q[u] = 0.0f;
-            if (s < s_hi) {
-                bool bad = false;
-                float z = pt::orbit_z(r, dt + ss_offset(t_exp, s, nss), max_iter, &bad);
-                if (bad) ++*nbad;
-                if (z < 1.0f + kk) {
-                    float c = z / (1.0f + kk);
-                    x[u] = c * c;
-                    q[u] = sqrtf((1.0f - c) * (1.0f + c));
-                }
-            }
-            any |= q[u] > 0.0f;
-        }
-        if (!any) continue;   // every supersample of this block is out of transit
-#pragma unroll 1
-        for (int n = 0; n < NP1; ++n) {
-            const float4 *tab = stab + n * n_j;
-            float b1[SB], b2v[SB];
-            if constexpr (SB % 2 == 0) {
-                unsigned long long xp[SB / 2], bp1[SB / 2], bp2[SB / 2];
-#pragma unroll
-                for (int p = 0; p < SB / 2; ++p) {
-                    xp[p] = f2_pack(x[2 * p], x[2 * p + 1]);
-                    bp1[p] = 0ull;
-                    bp2[p] = 0ull;
-                }
-#pragma unroll 8
-                for (int j = n_j - 1; j >= 0; --j) {
-                    float4 c = tab[j];
-                    unsigned long long cx = f2_pack(c.x, c.x), cy = f2_pack(c.y, c.y);
-                    unsigned long long cz = f2_pack(c.z, c.z), cw = f2_pack(c.w, c.w);
-#pragma unroll
-                    for (int p = 0; p < SB / 2; ++p) {
-                        unsigned long long al = f2_fma(cy, xp[p], cx);
-                        unsigned long long t = f2_fma(cz, bp2[p], cw);
-                        unsigned long long bj = f2_fma(al, bp1[p], t);
-                        bp2[p] = bp1[p];
-                        bp1[p] = bj;
-                    }
-                }
-#pragma unroll
-                for (int p = 0; p < SB / 2; ++p) f2_split(bp1[p], b1[2 * p], b1[2 * p + 1]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < SB; ++u) {
-                    b1[u] = 0.0f;
-                    b2v[u] = 0.0f;
-                }
-#pragma unroll 8
-                for (int j = n_j - 1; j >= 0; --j) {
-                    float4 c = tab[j];
-#pragma unroll
-                    for (int u = 0; u < SB; ++u) {
-                        float al = fmaf(c.y, x[u], c.x);
-                        float t = fmaf(c.z, b2v[u], c.w);
-                        float bj = fmaf(al, b1[u], t);
-                        b2v[u] = b1[u];
-                        b1[u] = bj;
-                    }
-                }
-            }
-            float acc = 0.0f;
-#pragma unroll
-            for (int u = 0; u < SB; ++u) {
-                float qq = q[u] * q[u];
-                float pw = qq * qq;
-                for (int i = 0; i < n; ++i) pw *= q[u];
-                acc = fmaf(b2 * pw, b1[u], acc);
-            }
-            salpha[n][col] += acc;
-        }
-    }
-}
-
-template <int SB>
-__global__ void __launch_bounds__(GS_THREADS, GS_MIN_CTAS) gim_series_kernel(GimArgs A)
-{
-    extern __shared__ __align__(16) unsigned char dsm[];
-    float4 *stab = reinterpret_cast<float4 *>(dsm);   // [N+1][n_j]
-    __shared__ GeomRec srec;
-    __shared__ float salpha[G_MAX_NP1][GS_THREADS];
-    __shared__ int sitem, sgeom, sbad;
-
-    const int NP1 = A.N + 1;
-    const int nj = A.n_j;
-    const int nss = A.n_ss;
-    const int ppi = A.ppi;
-    const int tid = threadIdx.x;
-    const bool split = ppi < GS_THREADS;   // two threads per pair
-    const int half = split ? tid / ppi : 0;
-    const int pl = tid - half * ppi;
-    const int s_mid = (nss + 1) / 2;
-    const int s_lo = (split && half) ? s_mid : 0;
-    const int s_hi = (split && !half) ? s_mid : nss;
-    const int total = A.pref[A.n_geom];
-    const float inv_nss = 1.0f / (float)nss;
-    int nbad = 0;
-    int staged = -1;
-    if (tid == 0) sbad = 0;
-
-#pragma unroll 1
-    for (;;) {
-        if (tid == 0) {
-            int it = atomicAdd(A.ctr, 1);
-            int g = -1;
-            if (it < total) {   // the largest g with pref[g] <= it
-                int lo = 0, hi = A.n_geom - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (A.pref[mid] <= it) lo = mid;
-                    else hi = mid - 1;
-                }
-                g = lo;
-            }
-            sitem = it;
-            sgeom = g;
-        }
-        __syncthreads();
-        const int it = sitem;
-        const int g = sgeom;
-        if (it >= total) break;   // uniform over the CTA
-        if (g != staged) {
-            const float4 *src = A.gtab + (size_t)g * NP1 * nj;
-            for (int i = tid; i < NP1 * nj; i += GS_THREADS) stab[i] = src[i];
-            if (tid < 6) reinterpret_cast<float4 *>(&srec)[tid] = reinterpret_cast<const float4 *>(&A.rec[g])[tid];
-            staged = g;
-        }
-        for (int n = 0; n < NP1; ++n) salpha[n][tid] = 0.0f;
-        __syncthreads();
-        const int i = (it - A.pref[g]) * ppi + pl;
-        const bool valid = i < A.cnt[g];
-        const int t = valid ? A.list[(size_t)g * A.n_t + i] : 0;
-        if (valid && s_lo < s_hi) {
-            float2 ts = A.tsplit[t];
-            float dt = pt::reduce_time(ts.x, ts.y, srec);
-            gim_pair<SB>(stab, NP1, nj, srec, dt, A.t_exp, nss, s_lo, s_hi, A.max_iter, salpha, tid, &nbad);
-        }
-        __syncthreads();
-        if (valid && half == 0) {
-#pragma unroll 1
-            for (int bb = 0; bb < A.n_bpg; ++bb) {
-                size_t row = (size_t)g * A.n_bpg + bb;
-                const float *u = A.ld + row * A.N;
-                // C_0 = (1 - sum u)/D, C_n = u_n/D, D = 1 - sum n u_n/(n+2)   (Sec. 2.1.3)
-                float su = 0.0f, sd = 0.0f;
-                for (int n = 1; n <= A.N; ++n) {
-                    float un = u[n - 1];
-                    su += un;
-                    sd += (float)n * un / (float)(n + 2);
-                }
-                float a0 = salpha[0][pl] + (split ? salpha[0][pl + ppi] : 0.0f);
-                float al = (1.0f - su) * a0;
-                for (int n = 1; n <= A.N; ++n) {
-                    float an = salpha[n][pl] + (split ? salpha[n][pl + ppi] : 0.0f);
-                    al = fmaf(u[n - 1], an, al);
-                }
-                A.flux[row * A.n_t + t] = 1.0f - al / (1.0f - sd) * inv_nss;
-            }
-        }
-    }
-    if (nbad) atomicAdd(&sbad, nbad);
-    __syncthreads();
-    if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
-}
-
-size_t gim_series_smem(int N, int n_j) { return (size_t)(N + 1) * n_j * sizeof(float4); }
 
 // ---------------------------------------------------------------------------
 // Chebyshev form of the series.  For one geometry and order n,
@@ -1637,32 +1446,6 @@ void jacobi_rec(double p, double q, int j, double *r)
 }  // namespace
 
 namespace {
-// Persistent launch of the series kernel: as many CTAs as fit on the GPU at
-// once (never more than there can be work items).
-template <int SB>
-int launch_series(const GimArgs &A, size_t smem, size_t max_items, cudaStream_t s)
-{
-    static thread_local size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(gim_series_kernel<SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return set_cuda_error(e, "gim_series_kernel smem attribute");
-        configured = smem;
-    }
-    int dev = 0, n_sm = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gim_series_kernel<SB>, GS_THREADS, smem);
-    if (e != cudaSuccess) return set_cuda_error(e, "gim_series_kernel occupancy");
-    if (per_sm < 1) return pt_internal::set_error(PT_ERR_ARG, "gim_series_kernel", "does not fit on an SM");
-    size_t grid = (size_t)n_sm * per_sm;
-    if (grid > max_items) grid = max_items;
-    if (grid < 1) grid = 1;
-    gim_series_kernel<SB><<<(unsigned)grid, GS_THREADS, smem, s>>>(A);
-    return check_launch("gim_series_kernel");
-}
-
 int launch_zi(const GimArgs &A, const float *atab, int n_in, int n_edge, size_t smem, size_t max_items,
               cudaStream_t s)
 {
@@ -1684,10 +1467,6 @@ int launch_zi(const GimArgs &A, const float *atab, int n_in, int n_edge, size_t 
     gim_zi_kernel<<<(unsigned)grid, GS_THREADS, smem, s>>>(A, atab, n_in, n_edge);
     return check_launch("gim_zi_kernel");
 }
-
-// The series evaluated in its Chebyshev form (gim_cheb_kernel) instead of
-// gim_series_kernel's per-order Clenshaw summation.
-constexpr bool G_CHEB = true;
 
 template <int NPAIR>
 int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab,
@@ -2190,7 +1969,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     const int NP1 = plan->N + 1;
     WorkLayout L = work_layout(n_t, orb->n_v, n_b, k_per_band, NP1, plan->n_j, zi ? n_in + n_edge : 0);
     if (work_bytes < L.total) return PT_ERR_WORKSPACE;
-    const size_t smem = zi ? gim_zi_smem(plan->N, n_in + n_edge) : gim_series_smem(plan->N, plan->n_j);
+    const size_t smem = zi ? gim_zi_smem(plan->N, n_in + n_edge) : gim_cheb_smem(plan->n_j, (plan->N + 2) / 2);
     if (smem > 200 * 1024) return PT_ERR_ARG;
     const int n_geom = k_per_band ? orb->n_v * n_b : orb->n_v;
     const int n_tiles = (n_t + TT - 1) / TT;
@@ -2224,10 +2003,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     A.pref = (int *)(wb + L.pref);
     A.ctr = cnt + n_geom;
     A.list = (int *)(wb + L.list);
-    // items of GS_THREADS listed pairs; only the per-order series kernel
-    // splits a long supersample list over two threads per pair
-    const bool cheb = !zi && G_CHEB;
-    A.ppi = (!zi && !cheb && n_ss >= 20) ? GS_THREADS / 2 : GS_THREADS;
+    A.ppi = GS_THREADS;   // work items of GS_THREADS listed pairs
     A.n_bad = n_bad;
     TableJob J;
     J.rec = rec;
@@ -2263,31 +2039,11 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, A.ppi, A.pref, A.ctr);
     st = check_launch("gim_scan_kernel");
     if (st) return st;
-    // supersamples per thread: h = n_ss, or half of it when two threads
-    // share a pair; blocks of SB = 1 without supersampling, else an even SB
-    // (two supersamples per two-lane FMA) with the least masked tail
-    const int h = (A.ppi < GS_THREADS) ? (n_ss + 1) / 2 : n_ss;
-    const size_t max_items = (size_t)n_geom * ((n_t + A.ppi - 1) / A.ppi);
+    const size_t max_items = (size_t)n_geom * ((n_t + GS_THREADS - 1) / GS_THREADS);
     if (zi)
         st = launch_zi(A, atab, n_in, n_edge, smem, max_items, s);
-    else if (cheb)
-        st = launch_cheb(A, T, plan->d_cx, plan->d_ccos, dtab, (size_t)n_geom * ((n_t + GS_THREADS - 1) / GS_THREADS), s);
-    else if (h == 1)
-        st = launch_series<1>(A, smem, max_items, s);
-    else if (h <= 2)
-        st = launch_series<2>(A, smem, max_items, s);
-    else if (h <= 4)
-        st = launch_series<4>(A, smem, max_items, s);
-    else if (h <= 6)
-        st = launch_series<6>(A, smem, max_items, s);
-    else if (h <= 8)
-        st = launch_series<8>(A, smem, max_items, s);
-    else if (h % 10 == 0 || h % 10 > 8)
-        st = launch_series<10>(A, smem, max_items, s);
-    else if (h % 8 == 0 || h % 8 > 6)
-        st = launch_series<8>(A, smem, max_items, s);
     else
-        st = launch_series<6>(A, smem, max_items, s);
+        st = launch_cheb(A, T, plan->d_cx, plan->d_ccos, dtab, max_items, s);
     if (st) return st;
     if (ssr) {
         ssr_rows_kernel<<<orb->n_v * n_b, 256, 0, s>>>(A.flux, y, wt, n_t, n_b, ssr);

@@ -182,3 +182,20 @@ def test_time_order_does_not_matter(torch_cuda, order):
     assert (ref_m < 1).sum() > 0
     assert np.max(np.abs(fm.cpu().numpy() - ref_m)) <= TOL
     assert np.max(np.abs(fg.cpu().numpy() - ref_g)) <= TOL
+
+
+@pytest.mark.parametrize("k_scale", [0.3, 0.45])
+def test_gimenez_large_radius_ratio(torch_cuda, k_scale):
+    """Radius ratios beyond the long-cadence prior (where the series values
+    and their Chebyshev coefficients are largest relative to the result)."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=4, n_t=1200, n_ss=5, cadence=0.01)
+    wl["k"] = np.full(4, k_scale) * np.array([0.9, 0.95, 1.0, 1.05])
+    wl["ld"] = wl["ld_gim"]
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(8, 128)
+    flux, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=5, t_exp=wl["t_exp"])
+    ref = _oracle_lc(wl, 128)
+    assert (ref < 1).sum() > 0
+    assert np.max(np.abs(flux.cpu().numpy() - ref)) <= TOL
