@@ -664,7 +664,7 @@ def main():
                 "max_abs_err_vs_oracle": max_err,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "ma_interp": ma_interp, "gimenez_zi": gim_zi, "adjoint": adjoint,
                 "batched": batched, "surrogate": surrogate,
-                "gpu_launches": 8 * K, "clocks": dict(clocks, window="%.1f s of untimed steps + the timed region"
+                "gpu_launches": 9 * K, "clocks": dict(clocks, window="%.1f s of untimed steps + the timed region"
                                                       % args.heat_s) if clocks else None,
                 "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
