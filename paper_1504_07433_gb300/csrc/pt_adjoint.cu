@@ -244,7 +244,7 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
     float sh, ch;
     bool conv = false;
     for (int it = 0; it < max_iter; ++it) {
-        sincosf(0.5f * dE, &sh, &ch);
+        pt::sincos_near0(0.5f * dE, &sh, &ch);
         float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
         float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
         float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
@@ -256,7 +256,7 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
         }
     }
     if (!conv) *bad = true;
-    sincosf(0.5f * dE, &sh, &ch);
+    pt::sincos_near0(0.5f * dE, &sh, &ch);
     float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
     float dC = -r.cE * omc - r.sE * sn;
     float dS = r.cE * sn - r.sE * omc;

@@ -79,6 +79,28 @@ __device__ __forceinline__ bool maybe_in_window(float th, const GeomRec &r)
     return (d + m >= r.win_lo) && (d - m <= r.win_hi);
 }
 
+// sin h and cos h by their Taylor series through h^9 and h^10, for the
+// small angles of the transit window (|h| <= 0.4: the first omitted terms,
+// h^11/11! and h^12/12!, are below 1e-11 relative); other angles take
+// sincosf.
+__device__ __forceinline__ void sincos_near0(float h, float *s, float *c)
+{
+    if (fabsf(h) <= 0.4f) {
+        const float h2 = h * h;
+        float ps = fmaf(h2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+        ps = fmaf(h2, ps, 1.0f / 120.0f);
+        ps = fmaf(h2, ps, -1.0f / 6.0f);
+        *s = fmaf(h * h2, ps, h);
+        float pc = fmaf(h2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+        pc = fmaf(h2, pc, -1.0f / 720.0f);
+        pc = fmaf(h2, pc, 1.0f / 24.0f);
+        pc = fmaf(h2, pc, -0.5f);
+        *c = fmaf(h2, pc, 1.0f);
+    } else {
+        sincosf(h, s, c);
+    }
+}
+
 // Projected separation z at time offset dt from conjunction (Sec. 1; the
 // paper prints no orbit formula).
 //   Circular:  phi = 2 pi dt / P,  z = a sqrt(sin^2 phi + cos^2 i cos^2 phi).
@@ -101,7 +123,7 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
 {
     if (r.ecc == 0.0f) {
         float s, c;
-        sincosf(r.nang * dt, &s, &c);
+        sincos_near0(r.nang * dt, &s, &c);
         if (c <= 0.0f) return PT_ZBEHIND;
         float ci = r.cosi * c;
         return r.a * (FAST ? fast_sqrt(fmaf(s, s, ci * ci)) : sqrtf(fmaf(s, s, ci * ci)));
@@ -111,7 +133,7 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
     float sh, ch;
     bool conv = false;
     for (int it = 0; it < max_iter; ++it) {
-        sincosf(0.5f * dE, &sh, &ch);
+        sincos_near0(0.5f * dE, &sh, &ch);
         float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
         float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
         float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
@@ -123,7 +145,7 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
         }
     }
     if (!conv) *bad = true;
-    sincosf(0.5f * dE, &sh, &ch);
+    sincos_near0(0.5f * dE, &sh, &ch);
     float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
     float dC = -r.cE * omc - r.sE * sn;
     float dS = r.cE * sn - r.sE * omc;
