@@ -690,12 +690,27 @@ __global__ void __launch_bounds__(128) gim_cheb_coef_kernel(const float4 *gtab, 
             sS[2 * i + o] = c1;
         }
     }
+    // cos(pi m (n_j - i - 1/2) / n_j) = (-1)^m cos(pi m (i + 1/2) / n_j): the
+    // transform needs the first ceil(n_j / 2) nodes only, applied to
+    // S_i + S_{n_j-1-i} for even m and S_i - S_{n_j-1-i} for odd m (for odd
+    // n_j the middle node pairs with itself; its cosine vanishes for odd m)
+    const int H = (n_j + 1) / 2;
+    float4 *sPM = reinterpret_cast<float4 *>(((uintptr_t)(scos + CC_CI * n_j) + 15) & ~(uintptr_t)15);
+    // sPM[H]: (S+ order 0, S+ order 1, S- order 0, S- order 1), 16-byte aligned
+    __syncthreads();
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        const int j = n_j - 1 - i;
+        float2 a = reinterpret_cast<const float2 *>(sS)[i];
+        float2 b = reinterpret_cast<const float2 *>(sS)[j];
+        sPM[i] = (i == j) ? make_float4(a.x, a.y, 0.0f, 0.0f)
+                          : make_float4(a.x + b.x, a.y + b.y, a.x - b.x, a.y - b.y);
+    }
     float sum[CC_MR][2], err[CC_MR][2];
 #pragma unroll
     for (int r = 0; r < CC_MR; ++r) sum[r][0] = sum[r][1] = err[r][0] = err[r][1] = 0.0f;
     if (no > 0) {
-        for (int i0 = 0; i0 < n_j; i0 += CC_CI) {
-            const int ci = min(CC_CI, n_j - i0);
+        for (int i0 = 0; i0 < H; i0 += CC_CI) {
+            const int ci = min(CC_CI, H - i0);
             __syncthreads();
             if ((n_j & 3) == 0) {   // 128-bit copies, issued together
                 const float4 *cs4 = reinterpret_cast<const float4 *>(ccos + (size_t)i0 * n_j);
@@ -712,9 +727,11 @@ __global__ void __launch_bounds__(128) gim_cheb_coef_kernel(const float4 *gtab, 
             for (int r = 0; r < CC_MR; ++r) {
                 const int m = threadIdx.x + r * blockDim.x;
                 if (m >= n_j) break;
+                const bool odd = m & 1;
                 for (int ii = 0; ii < ci; ++ii) {
                     const float a = scos[ii * n_j + m];
-                    const float2 v2 = reinterpret_cast<const float2 *>(sS)[i0 + ii];
+                    const float4 pm = sPM[i0 + ii];
+                    const float2 v2 = odd ? make_float2(pm.z, pm.w) : make_float2(pm.x, pm.y);
 #pragma unroll
                     for (int o = 0; o < 2; ++o) {
                         const float v = o ? v2.y : v2.x;
@@ -740,8 +757,10 @@ __global__ void __launch_bounds__(128) gim_cheb_coef_kernel(const float4 *gtab, 
 
 size_t gim_cheb_coef_smem(int n_j)
 {
-    // two orders' table rows and node values, and a chunk of the cosine table
-    return (size_t)n_j * (2 * sizeof(float4) + 2 * sizeof(float) + CC_CI * sizeof(float));
+    // two orders' table rows and node values, a chunk of the cosine table,
+    // and the symmetric and antisymmetric node sums
+    return (size_t)n_j * (2 * sizeof(float4) + 2 * sizeof(float) + CC_CI * sizeof(float)) +
+           (size_t)((n_j + 1) / 2) * sizeof(float4) + 16;
 }
 
 // Evaluation over the pair lists: persistent CTAs take items of GS_THREADS

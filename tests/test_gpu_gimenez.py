@@ -199,3 +199,20 @@ def test_gimenez_large_radius_ratio(torch_cuda, k_scale):
     ref = _oracle_lc(wl, 128)
     assert (ref < 1).sum() > 0
     assert np.max(np.abs(flux.cpu().numpy() - ref)) <= TOL
+
+
+@pytest.mark.parametrize("N,n_j", [(8, 97), (8, 98), (5, 33)])
+def test_gimenez_series_depths(torch_cuda, N, n_j):
+    """Series depths that are odd (the middle Chebyshev node pairs with
+    itself in the transform) or not a multiple of four (scalar copies of the
+    cosine table)."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=3, n_t=1000, n_ss=4, cadence=0.01, n_gim=N)
+    wl["ld"] = wl["ld_gim"]
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(N, n_j)
+    flux, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=4, t_exp=wl["t_exp"])
+    ref = _oracle_lc(wl, n_j)
+    assert (ref < 1).sum() > 0
+    assert np.max(np.abs(flux.cpu().numpy() - ref)) <= TOL
