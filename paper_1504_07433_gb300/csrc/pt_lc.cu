@@ -406,10 +406,13 @@ __device__ __forceinline__ DF df_mul(DF a, DF b)
 // z-recursion coefficients r1_j, r2_j, r3_{j+1} of G_j(nu+2, 1; x) with
 // T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2, the z-independent factor of
 // Sec. 2.1.4 (recursion in double-float arithmetic, stored FP32).
-// A table CTA covers one order n and TT geometries; row n of the plan's
-// coefficients is staged in shared memory as double-float pairs.  The
-// recursion is a chain of n_j dependent steps per thread, so the table CTAs
-// run inside the window kernel's launch, in the shadow of its wide grid.
+// A table CTA covers one order n and TABLE_GPC geometries (one thread each;
+// the CTA's other threads only help stage row n of the plan's coefficients
+// in shared memory as double-float pairs).  The recursion is a chain of n_j
+// dependent steps per thread, so the chains are spread thinly over many SMs,
+// and the table CTAs run inside the window kernel's launch, in the shadow of
+// its wide grid.
+constexpr int TABLE_GPC = 64;
 struct TableJob {
     const GeomRec *rec;
     int n_geom, NP1, n_j;
@@ -432,8 +435,8 @@ __device__ __forceinline__ void table_cta(const TableJob &J, int n, int gb)
     }
     for (int i = threadIdx.x; i < 3 * n_j; i += blockDim.x) srb[i] = df_of(J.recb[(size_t)n * n_j * 3 + i]);
     __syncthreads();
-    const int g = gb * blockDim.x + threadIdx.x;
-    if (g >= J.n_geom) return;
+    const int g = gb * TABLE_GPC + threadIdx.x;
+    if (threadIdx.x >= TABLE_GPC || g >= J.n_geom) return;
     const double k = J.rec[g].k;
     const DF x = df_of(1.0 - k / (1.0 + k));
     float4 *out = J.tab + ((size_t)g * J.NP1 + n) * n_j;
@@ -2033,7 +2036,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     J.recb = plan->d_recb;
     J.coef = plan->d_coef;
     J.tab = T;
-    J.n_blocks = NP1 * ((n_geom + TT - 1) / TT);
+    J.n_blocks = NP1 * ((n_geom + TABLE_GPC - 1) / TABLE_GPC);
     const size_t tsm = gim_table_smem(plan->n_j);
     if (tsm > 48 * 1024) {
         static thread_local size_t tsm_configured = 0;
