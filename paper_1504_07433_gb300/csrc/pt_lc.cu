@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 // ---------------------------------------------------------------------------
 constexpr int GW_VT = 32;         // geometries per CTA of the window kernel (<= 32: one bit each)
 constexpr int GS_THREADS = 128;   // threads per CTA of the evaluation kernels (one pair each)
+constexpr int GS_PAIRS = 2;       // register pairs of supersamples per coefficient load (Chebyshev kernel)
 
 struct GimArgs {
     const float2 *tsplit;
@@ -611,29 +612,10 @@ __global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_ge
     if (threadIdx.x == 0) pref[n_geom] = scarry;
 }
 
-// Two-lane FP32 arithmetic (sm_100 family): a 64-bit register holds two
-// floats and one fma.rn.f32x2 performs both lanes' FMAs, each rounded like
-// fmaf.  The Chebyshev evaluation keeps two orders of the series in the two
-// lanes.
-__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
-{
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-
-__device__ __forceinline__ void f2_split(unsigned long long v, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c)
-{
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
+// Two-lane FP32 arithmetic (sm_100 family): __ffma2_rn performs the FMAs of
+// both lanes of a float2 in one instruction, each rounded like fmaf.  The
+// Chebyshev evaluation keeps two supersamples in the two lanes.
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 
 // ---------------------------------------------------------------------------
@@ -646,8 +628,7 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
 // (the discrete cosine transform of the node values; exact for a polynomial
 // of that degree).  The Chebyshev basis does not depend on n, so one
 // recurrence T_{m+1} = 2y T_m - T_{m-1} per supersample serves all N + 1
-// orders, and the orders accumulate two at a time in two-lane FMAs: about
-// (N + 3) FMAs per term instead of 3 (N + 1).
+// orders: N + 2 FMAs per term instead of 3 (N + 1).
 // gim_cheb_coef_kernel: one CTA per geometry; node values by the same
 // Clenshaw summation as the series kernel (FP32), then the transform with
 // compensated sums (each product and its FMA-exact error added by a two-sum).
@@ -655,7 +636,8 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
 // One CTA per (geometry, pair of orders), so that enough warps hide the
 // dependent chains: the node values of the two orders, then their two
 // coefficient rows (one thread per m, cosine table through shared memory).
-// Orders past N (padding of the coefficient rows) get zeros.
+// Each coefficient row holds s_m d_{n,m} twice per order (see the evaluation
+// kernel); an order past N (padding of the row) gets zeros.
 constexpr int CC_CI = 16;   // cosine-table rows per shared-memory chunk
 constexpr int CC_MR = 4;    // coefficient rows per thread: n_j <= CC_MR * 128
 
@@ -753,8 +735,10 @@ __global__ void __launch_bounds__(128) gim_cheb_coef_kernel(const float4 *gtab, 
     for (int r = 0; r < CC_MR; ++r) {
         const int m = threadIdx.x + r * blockDim.x;
         if (m >= n_j) break;
-        float2 o2 = make_float2(no > 0 ? sum[r][0] + err[r][0] : 0.0f, no > 1 ? sum[r][1] + err[r][1] : 0.0f);
-        reinterpret_cast<float2 *>(dtab + ((size_t)g * n_j + m) * DS)[blockIdx.y] = o2;
+        const float sg = (m & 2) ? -1.0f : 1.0f;   // s_m: +, +, -, -, ...
+        const float v0 = no > 0 ? sg * (sum[r][0] + err[r][0]) : 0.0f;
+        const float v1 = no > 1 ? sg * (sum[r][1] + err[r][1]) : 0.0f;
+        reinterpret_cast<float4 *>(dtab + ((size_t)g * n_j + m) * DS)[blockIdx.y] = make_float4(v0, v0, v1, v1);
     }
 }
 
@@ -766,27 +750,98 @@ size_t gim_cheb_coef_smem(int n_j)
            (size_t)((n_j + 1) / 2) * sizeof(float4) + 16;
 }
 
-// Evaluation over the pair lists: persistent CTAs take items of GS_THREADS
-// listed pairs and stage the geometry's coefficients d[m][n] (n padded to an
-// even count) once per item; each thread evaluates its pair's in-transit
-// supersamples one by one (x = c^2, q = sqrt(1 - x), y = 2x - 1), with the
-// Chebyshev recurrence in one lane pair and NPAIR two-lane accumulators for
-// orders (2p, 2p+1), whose coefficient pairs load from shared memory as
-// 64-bit operands.  alpha_n = b^2 q^(n+4) S_n is summed over the supersamples
-// in order, then the passband combination of Sec. 2.1.3.
-template <int NPAIR>
+// Evaluation over the pair lists.  Persistent CTAs take items of GS_THREADS
+// listed pairs of one geometry and stage its coefficient rows once per item.
+// An item runs in batches of up to GS_SSB supersamples:
+//  1. each thread (one pair) computes z at the batch's supersamples and keeps
+//     the in-transit ones, (y = 2x - 1, q = sqrt(1 - x)) with x = c^2, in
+//     order; a scan over the CTA places every pair's entries in one dense
+//     list (pair-major, supersample-minor);
+//  2. the list is cut into chunks of 2 E GS_THREADS entries; each thread
+//     evaluates 2 E consecutive entries, whatever pairs they belong to, so
+//     that no lane idles on an out-of-transit supersample.  One 64-bit
+//     register holds two entries: one two-lane FMA advances both Chebyshev
+//     recurrences, one two-lane FMA per order n accumulates d_{n,m} T_m for
+//     both (the coefficient rows hold each d_{n,m} twice, one per lane).  The
+//     rows also carry the sign s_m = +1, +1, -1, -1, ... (period 4): with
+//     W_m = s_m T_m the recurrence reads W_{m+1} = (-1)^(m+1) 2y W_m + W_{m-1},
+//     an FMA with no negated operand, and s_m d_{n,m} W_m = d_{n,m} T_m
+//     exactly.  The S_n go to shared memory;
+//  3. each thread adds its own pair's b^2 q^(n+4) S_n to alpha_n in
+//     supersample order, so the sums do not depend on the chunking.
+// After the last batch, the passband combination of Sec. 2.1.3.
+constexpr int GS_SSB = 16;   // supersamples per batch of the Chebyshev kernel
+
+template <int NP1, int E>
+__device__ __forceinline__ void cheb_eval(const float *sd, int nj, const float (&y)[2 * E],
+                                          float2 (&acc)[E][NP1])
+{
+    constexpr int DS = 4 * ((NP1 + 1) / 2);
+    float2 wa[E], wb[E], ap[E], an[E];
+    {
+        const float2 *d0 = reinterpret_cast<const float2 *>(sd);
+        const float2 *d1 = reinterpret_cast<const float2 *>(sd + DS);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float a0 = y[2 * e] + y[2 * e], a1 = y[2 * e + 1] + y[2 * e + 1];
+            ap[e] = make_float2(a0, a1);
+            an[e] = make_float2(-a0, -a1);
+            wa[e] = make_float2(1.0f, 1.0f);
+            wb[e] = make_float2(y[2 * e], y[2 * e + 1]);
+#pragma unroll
+            for (int n = 0; n < NP1; ++n) acc[e][n] = f2_fma(d1[n], wb[e], d0[n]);
+        }
+    }
+    // one step: W_m from W_{m-1}, W_{m-2}, in place of W_{m-2} (wa for even
+    // m, wb for odd m, so the loop carries no register copies); negative
+    // multiplier for even m
+    auto step = [&](int m, const float2 (&cm)[E], float2 (&wn)[E],
+                    const float2 (&wp)[E]) {
+        float2 dm[NP1];
+        const float4 *row = reinterpret_cast<const float4 *>(sd + m * DS);
+#pragma unroll
+        for (int n = 0; n + 1 < NP1; n += 2) {
+            const float4 v = row[n / 2];
+            dm[n] = make_float2(v.x, v.y);
+            dm[n + 1] = make_float2(v.z, v.w);
+        }
+        if (NP1 & 1) dm[NP1 - 1] = reinterpret_cast<const float2 *>(row)[NP1 - 1];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            wn[e] = f2_fma(cm[e], wp[e], wn[e]);
+#pragma unroll
+            for (int n = 0; n < NP1; ++n) acc[e][n] = f2_fma(dm[n], wn[e], acc[e][n]);
+        }
+    };
+    int m = 2;
+#pragma unroll 1
+    for (; m + 1 < nj; m += 2) {
+        step(m, an, wa, wb);
+        step(m + 1, ap, wb, wa);
+    }
+    if (m < nj) step(m, an, wa, wb);
+}
+
+template <int NP1, int E>
 __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const float *dtab)
 {
-    constexpr int DS = (2 * NPAIR + 3) & ~3;   // floats per coefficient row
-    constexpr int SG = 2;                       // supersamples per group (share the coefficient loads)
-    extern __shared__ __align__(16) unsigned char dsm[];
-    float *sd = reinterpret_cast<float *>(dsm);   // [n_j][DS]
-    __shared__ GeomRec srec;
-    __shared__ int sitem, sgeom, sbad;
-    const int NP1 = A.N + 1;
+    constexpr int DS = 4 * ((NP1 + 1) / 2);   // floats per coefficient row
+    constexpr int G = 2 * E;                  // entries per thread and chunk
+    constexpr int CH = G * GS_THREADS;        // entries per chunk
+    static_assert(G == 2 || G == 4, "two or four entries per thread");
     const int nj = A.n_j;
     const int nss = A.n_ss;
+    const int ssb = min(nss, GS_SSB);
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float *sd = reinterpret_cast<float *>(dsm);                  // [n_j][DS] coefficient rows
+    float *sS = sd + nj * DS;                                    // [NP1][CH] series values of a chunk
+    float2 *syq = reinterpret_cast<float2 *>(sS + NP1 * CH);     // [GS_THREADS][ssb] (y, q) per pair
+    __shared__ GeomRec srec;
+    __shared__ int sitem, sgeom, sbad;
+    __shared__ int sst[GS_THREADS + 1];   // first dense entry of each pair; sst[GS_THREADS] = entries
+    __shared__ int swarp[GS_THREADS / 32];
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int total = A.pref[A.n_geom];
     const float inv_nss = 1.0f / (float)nss;
     int nbad = 0;
@@ -822,88 +877,113 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
         }
         __syncthreads();
         const int i = (it - A.pref[g]) * GS_THREADS + tid;
-        if (i < A.cnt[g]) {
-            const int t = A.list[(size_t)g * A.n_t + i];
-            float2 ts = A.tsplit[t];
-            const float dt = pt::reduce_time(ts.x, ts.y, srec);
-            const float kk = srec.k;
-            const float bk = kk / (1.0f + kk);
-            const float b2 = bk * bk;
-            unsigned long long aa[NPAIR];   // alpha sums over the supersamples, orders (2p, 2p+1)
+        const bool own = i < A.cnt[g];
+        const int t = own ? A.list[(size_t)g * A.n_t + i] : 0;
+        float dt = 0.0f;
+        if (own) {
+            const float2 ts = A.tsplit[t];
+            dt = pt::reduce_time(ts.x, ts.y, srec);
+        }
+        const float kk = srec.k;
+        const float bk = kk / (1.0f + kk);
+        const float b2 = bk * bk;
+        float al[NP1];   // alpha sums over the supersamples
 #pragma unroll
-            for (int p = 0; p < NPAIR; ++p) aa[p] = 0ull;
+        for (int n = 0; n < NP1; ++n) al[n] = 0.0f;
 #pragma unroll 1
-            for (int s0 = 0; s0 < nss; s0 += SG) {
-                float y[SG], q[SG];
-                bool any = false;
-#pragma unroll
-                for (int u = 0; u < SG; ++u) {
-                    y[u] = 0.0f;   // out of transit: q = 0 gives the supersample weight 0
-                    q[u] = 0.0f;
-                    if (s0 + u < nss) {
-                        bool bad = false;
-                        float z = pt::orbit_z(srec, dt + ss_offset(A.t_exp, s0 + u, nss), A.max_iter, &bad);
-                        if (bad) ++nbad;
-                        if (z < 1.0f + kk) {
-                            const float c = z / (1.0f + kk);
-                            const float x = c * c;
-                            q[u] = sqrtf((1.0f - c) * (1.0f + c));
-                            y[u] = fmaf(2.0f, x, -1.0f);
-                        }
-                    }
-                    any |= q[u] > 0.0f;
-                }
-                if (!any) continue;
-                unsigned long long acc[SG][NPAIR];
-                float t0[SG], t1[SG];
-                {
-                    const unsigned long long *d0 = reinterpret_cast<const unsigned long long *>(sd);
-                    const unsigned long long *d1 = reinterpret_cast<const unsigned long long *>(sd + DS);
-#pragma unroll
-                    for (int u = 0; u < SG; ++u) {
-                        const unsigned long long ty = f2_pack(y[u], y[u]);
-#pragma unroll
-                        for (int p = 0; p < NPAIR; ++p) acc[u][p] = f2_fma(d1[p], ty, d0[p]);
-                        t0[u] = 1.0f;
-                        t1[u] = y[u];
-                    }
-                }
-#pragma unroll 2
-                for (int m = 2; m < nj; ++m) {
-                    unsigned long long dm[NPAIR];
-                    const ulonglong2 *row = reinterpret_cast<const ulonglong2 *>(sd + m * DS);
-#pragma unroll
-                    for (int p = 0; p + 1 < NPAIR; p += 2) {
-                        ulonglong2 v = row[p / 2];
-                        dm[p] = v.x;
-                        dm[p + 1] = v.y;
-                    }
-                    if (NPAIR & 1) dm[NPAIR - 1] = reinterpret_cast<const unsigned long long *>(row)[NPAIR - 1];
-#pragma unroll
-                    for (int u = 0; u < SG; ++u) {
-                        const float t2 = fmaf(y[u] + y[u], t1[u], -t0[u]);
-                        const unsigned long long tt = f2_pack(t2, t2);
-#pragma unroll
-                        for (int p = 0; p < NPAIR; ++p) acc[u][p] = f2_fma(dm[p], tt, acc[u][p]);
-                        t0[u] = t1[u];
-                        t1[u] = t2;
-                    }
-                }
-                // alpha_n = b^2 q^(n+4) S_n, summed over the supersamples in order
-#pragma unroll
-                for (int u = 0; u < SG; ++u) {
-                    const float qq = q[u] * q[u];
-                    float w = b2 * qq * qq;
-#pragma unroll
-                    for (int p = 0; p < NPAIR; ++p) {
-                        aa[p] = f2_fma(acc[u][p], f2_pack(w, w * q[u]), aa[p]);
-                        w *= qq;
+        for (int sb0 = 0; sb0 < nss; sb0 += ssb) {
+            // 1. in-transit supersamples of this pair, in order
+            int c = 0;
+            if (own) {
+                const int s1 = min(nss, sb0 + ssb);
+#pragma unroll 1
+                for (int s = sb0; s < s1; ++s) {
+                    bool bad = false;
+                    const float z = pt::orbit_z(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad);
+                    if (bad) ++nbad;
+                    if (z < 1.0f + kk) {
+                        const float cz = z / (1.0f + kk);
+                        const float x = cz * cz;
+                        syq[tid * ssb + c] = make_float2(fmaf(2.0f, x, -1.0f), sqrtf((1.0f - cz) * (1.0f + cz)));
+                        ++c;
                     }
                 }
             }
-            float al[2 * NPAIR];
+            // exclusive scan of the counts over the CTA
+            int incl = c;
 #pragma unroll
-            for (int p = 0; p < NPAIR; ++p) f2_split(aa[p], al[2 * p], al[2 * p + 1]);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) swarp[warp] = incl;
+            __syncthreads();
+            int base = 0;
+#pragma unroll
+            for (int w = 0; w < GS_THREADS / 32; ++w) base += (w < warp) ? swarp[w] : 0;
+            sst[tid] = base + incl - c;
+            if (tid == GS_THREADS - 1) sst[GS_THREADS] = base + incl;
+            __syncthreads();
+            const int n_e = sst[GS_THREADS];
+            const int my0 = sst[tid];
+#pragma unroll 1
+            for (int c0 = 0; c0 < n_e; c0 += CH) {
+                // 2. series values of G consecutive entries
+                const int e0 = c0 + G * tid;
+                if (e0 < n_e) {
+                    float y[G];
+                    int p = 0;
+                    {
+                        int lo = 0, hi = GS_THREADS - 1;   // the last pair with sst[p] <= e0
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (sst[mid] <= e0) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        p = lo;
+                    }
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        const int e = e0 + u;
+                        y[u] = 0.0f;
+                        if (e < n_e) {
+                            while (sst[p + 1] <= e) ++p;
+                            y[u] = syq[p * ssb + (e - sst[p])].x;
+                        }
+                    }
+                    float2 acc[E][NP1];
+                    cheb_eval<NP1, E>(sd, nj, y, acc);
+#pragma unroll
+                    for (int n = 0; n < NP1; ++n) {
+                        float v[G];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) { v[2 * e] = acc[e][n].x; v[2 * e + 1] = acc[e][n].y; }
+                        if (G == 4)
+                            reinterpret_cast<float4 *>(sS + n * CH)[tid] = make_float4(v[0], v[1], v[2], v[3]);
+                        else
+                            reinterpret_cast<float2 *>(sS + n * CH)[tid] = make_float2(v[0], v[1]);
+                    }
+                }
+                __syncthreads();
+                // 3. this pair's entries of the chunk, in supersample order:
+                //    alpha_n += b^2 q^(n+4) S_n
+                const int ea = max(my0, c0), eb = min(my0 + c, c0 + CH);
+#pragma unroll 1
+                for (int e = ea; e < eb; ++e) {
+                    const float qu = syq[tid * ssb + (e - my0)].y;
+                    const float qq = qu * qu;
+                    float w = b2 * qq * qq;
+#pragma unroll
+                    for (int n = 0; n < NP1; n += 2) {
+                        al[n] = fmaf(sS[n * CH + (e - c0)], w, al[n]);
+                        if (n + 1 < NP1) al[n + 1] = fmaf(sS[(n + 1) * CH + (e - c0)], w * qu, al[n + 1]);
+                        w *= qq;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (own) {
 #pragma unroll 1
             for (int bb = 0; bb < A.n_bpg; ++bb) {
                 size_t row = (size_t)g * A.n_bpg + bb;
@@ -917,8 +997,7 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
                 }
                 float acc_f = (1.0f - su) * al[0];
 #pragma unroll
-                for (int n = 1; n < 2 * NPAIR; ++n)
-                    if (n < NP1) acc_f = fmaf(u[n - 1], al[n], acc_f);
+                for (int n = 1; n < NP1; ++n) acc_f = fmaf(u[n - 1], al[n], acc_f);
                 A.flux[row * A.n_t + t] = 1.0f - acc_f / (1.0f - sdn) * inv_nss;
             }
         }
@@ -928,7 +1007,14 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
     if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
 }
 
-size_t gim_cheb_smem(int n_j, int NPAIR) { return (size_t)n_j * ((2 * NPAIR + 3) & ~3) * sizeof(float); }
+// floats per coefficient row: each of the N + 1 orders twice, padded to 16 bytes
+int gim_cheb_ds(int N) { return 4 * ((N + 2) / 2); }
+// coefficient rows, a chunk of series values and a batch of (y, q) entries
+size_t gim_cheb_smem(int n_j, int N, int n_ss)
+{
+    return ((size_t)n_j * gim_cheb_ds(N) + (size_t)(N + 1) * 2 * GS_PAIRS * GS_THREADS) * sizeof(float) +
+           (size_t)GS_THREADS * (n_ss < GS_SSB ? n_ss : GS_SSB) * sizeof(float2);
+}
 
 // ---------------------------------------------------------------------------
 // Gimenez model interpolated in z (Sec. 3.3).  gim_zi_table_kernel evaluates
@@ -1403,8 +1489,8 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
         off += align256((size_t)n_v * n_b * n_t * sizeof(float));
         L.atab = off;
         off += align256((size_t)n_geom * n_zi * NP1 * sizeof(float));
-        L.dtab = off;   // Chebyshev coefficients, orders padded to an even count
-        off += align256((size_t)n_geom * n_j * (((NP1 + 1) & ~1) + 3 & ~3) * sizeof(float));
+        L.dtab = off;   // Chebyshev coefficient rows: each order twice, padded to 16 bytes
+        off += align256((size_t)n_geom * n_j * (4 * ((NP1 + 1) / 2)) * sizeof(float));
     }
     L.total = off;
     return L;
@@ -1490,13 +1576,14 @@ int launch_zi(const GimArgs &A, const float *atab, int n_in, int n_edge, size_t 
     return check_launch("gim_zi_kernel");
 }
 
-template <int NPAIR>
+template <int NP1>
 int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab,
                   size_t max_items, cudaStream_t s)
 {
+    constexpr int E = GS_PAIRS;
     // coefficients: one CTA per (geometry, pair of orders), every row of
-    // DS floats written (orders past N as zeros)
-    constexpr int DS = (2 * NPAIR + 3) & ~3;
+    // DS floats written (an order past N as zeros)
+    constexpr int DS = 4 * ((NP1 + 1) / 2);
     const size_t csm = gim_cheb_coef_smem(A.n_j);
     static thread_local size_t csm_configured = 0;
     if (csm > 48 * 1024 && csm > csm_configured) {
@@ -1505,14 +1592,14 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const floa
         if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_coef_kernel smem attribute");
         csm_configured = csm;
     }
-    gim_cheb_coef_kernel<<<dim3(A.n_geom, DS / 2), 128, csm, s>>>(T, A.N + 1, A.n_j, DS, cx, ccos, dtab);
+    gim_cheb_coef_kernel<<<dim3(A.n_geom, DS / 4), 128, csm, s>>>(T, A.N + 1, A.n_j, DS, cx, ccos, dtab);
     int st = check_launch("gim_cheb_coef_kernel");
     if (st) return st;
     // evaluation: persistent
-    const size_t smem = gim_cheb_smem(A.n_j, NPAIR);
+    const size_t smem = gim_cheb_smem(A.n_j, A.N, A.n_ss);
     static thread_local size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(gim_cheb_kernel<NPAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(gim_cheb_kernel<NP1, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_kernel smem attribute");
         configured = smem;
@@ -1521,22 +1608,21 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const floa
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gim_cheb_kernel<NPAIR>, GS_THREADS, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gim_cheb_kernel<NP1, E>, GS_THREADS, smem);
     if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_kernel occupancy");
     if (per_sm < 1) return pt_internal::set_error(PT_ERR_ARG, "gim_cheb_kernel", "does not fit on an SM");
     size_t grid = (size_t)n_sm * per_sm;
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
-    gim_cheb_kernel<NPAIR><<<(unsigned)grid, GS_THREADS, smem, s>>>(A, dtab);
+    gim_cheb_kernel<NP1, E><<<(unsigned)grid, GS_THREADS, smem, s>>>(A, dtab);
     return check_launch("gim_cheb_kernel");
 }
 
-// Chebyshev path: coefficient and evaluation kernels, for NPAIR = ceil((N + 1) / 2).
+// Chebyshev path: coefficient and evaluation kernels, for N + 1 orders.
 int launch_cheb(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab, size_t max_items,
                 cudaStream_t s)
 {
-    switch ((A.N + 2) / 2) {
-    case 1: return launch_cheb_t<1>(A, T, cx, ccos, dtab, max_items, s);
+    switch (A.N + 1) {
     case 2: return launch_cheb_t<2>(A, T, cx, ccos, dtab, max_items, s);
     case 3: return launch_cheb_t<3>(A, T, cx, ccos, dtab, max_items, s);
     case 4: return launch_cheb_t<4>(A, T, cx, ccos, dtab, max_items, s);
@@ -1544,7 +1630,15 @@ int launch_cheb(const GimArgs &A, const float4 *T, const float *cx, const float 
     case 6: return launch_cheb_t<6>(A, T, cx, ccos, dtab, max_items, s);
     case 7: return launch_cheb_t<7>(A, T, cx, ccos, dtab, max_items, s);
     case 8: return launch_cheb_t<8>(A, T, cx, ccos, dtab, max_items, s);
-    default: return launch_cheb_t<9>(A, T, cx, ccos, dtab, max_items, s);
+    case 9: return launch_cheb_t<9>(A, T, cx, ccos, dtab, max_items, s);
+    case 10: return launch_cheb_t<10>(A, T, cx, ccos, dtab, max_items, s);
+    case 11: return launch_cheb_t<11>(A, T, cx, ccos, dtab, max_items, s);
+    case 12: return launch_cheb_t<12>(A, T, cx, ccos, dtab, max_items, s);
+    case 13: return launch_cheb_t<13>(A, T, cx, ccos, dtab, max_items, s);
+    case 14: return launch_cheb_t<14>(A, T, cx, ccos, dtab, max_items, s);
+    case 15: return launch_cheb_t<15>(A, T, cx, ccos, dtab, max_items, s);
+    case 16: return launch_cheb_t<16>(A, T, cx, ccos, dtab, max_items, s);
+    default: return launch_cheb_t<17>(A, T, cx, ccos, dtab, max_items, s);
     }
 }
 
@@ -1991,7 +2085,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     const int NP1 = plan->N + 1;
     WorkLayout L = work_layout(n_t, orb->n_v, n_b, k_per_band, NP1, plan->n_j, zi ? n_in + n_edge : 0);
     if (work_bytes < L.total) return PT_ERR_WORKSPACE;
-    const size_t smem = zi ? gim_zi_smem(plan->N, n_in + n_edge) : gim_cheb_smem(plan->n_j, (plan->N + 2) / 2);
+    const size_t smem = zi ? gim_zi_smem(plan->N, n_in + n_edge) : gim_cheb_smem(plan->n_j, plan->N, n_ss);
     if (smem > 200 * 1024) return PT_ERR_ARG;
     const int n_geom = k_per_band ? orb->n_v * n_b : orb->n_v;
     const int n_tiles = (n_t + TT - 1) / TT;
