@@ -225,7 +225,8 @@ __device__ void make_const(const pt_theta &th, int v, float half_exp, VecConst *
     }
     r.win_lo = lo;
     r.win_hi = hi;
-    r.pad0 = r.pad1 = r.pad2 = 0.0f;
+    r.nq = (float)(e / (1.0 - e));
+    r.pad1 = r.pad2 = 0.0f;
     c->k = k;
     c->u1 = th.u1[v];
     c->u2 = th.u2[v];

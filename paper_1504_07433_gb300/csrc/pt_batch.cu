@@ -168,11 +168,12 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
             for (int qi = tid; qi < nq; qi += TT) {
                 int tl = squeue[qi];
                 float le = 0.0f, ld = 0.0f, ed = 0.0f;
+                float warm[3] = {__int_as_float(0x7fffffff), 0.0f, 0.0f};   // Kepler warm start (none yet)
                 for (int s = 0; s < A.n_ss; ++s) {
                     float zs = sz[tl];
                     if (A.n_ss > 1) {
                         float dts = sdt[tl] + A.t_exp * (((float)s + 0.5f) * inv_ss - 0.5f);
-                        zs = pt::orbit_z<true>(srec, dts, A.max_iter, &bad);
+                        zs = pt::orbit_z<true>(srec, dts, A.max_iter, &bad, warm);
                     }
                     float a0, a1, a2;
                     pt::ma_terms(srec.k, zs, &a0, &a1, &a2);
@@ -202,9 +203,10 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
                 pt::ma_terms(kb, sz[tl], &le, &ld, &ed);
             } else {
                 le = ld = ed = 0.0f;
+                float warm[3] = {__int_as_float(0x7fffffff), 0.0f, 0.0f};   // Kepler warm start (none yet)
                 for (int s = 0; s < A.n_ss; ++s) {
                     float dts = sdt[tl] + A.t_exp * (((float)s + 0.5f) * inv_ss - 0.5f);
-                    float zs = pt::orbit_z<true>(srec, dts, A.max_iter, &bad);
+                    float zs = pt::orbit_z<true>(srec, dts, A.max_iter, &bad, warm);
                     float a0, a1, a2;
                     pt::ma_terms(kb, zs, &a0, &a1, &a2);
                     le += a0;

@@ -34,7 +34,7 @@ struct __align__(16) GeomRec {
     float a, cosi, k, ecc;    // a/R*, cos i, radius ratio, 0 = circular / 1 = eccentric
     float ecE, esE, cE, sE;   // e cos E_tr, e sin E_tr, cos E_tr, sin E_tr
     float Uc, Us, Vs, Vc;     // a cos w, a sqrt(1-e^2) sin w, a sin w, a sqrt(1-e^2) cos w
-    float Vtr, pad0, pad1, pad2;  // r at conjunction = a (1 - e cos E_tr)
+    float Vtr, nq, pad1, pad2;    // r at conjunction = a (1 - e cos E_tr); e / (1 - e) (Newton's error factor)
 };
 static_assert(sizeof(GeomRec) == 96, "GeomRec layout");
 
@@ -114,12 +114,20 @@ __device__ __forceinline__ void sincos_near0(float h, float *s, float *c)
 //     1 - cos dE = 2 sin^2(dE/2).  Every term is small near transit, so FP32
 //     keeps relative accuracy there; z = sqrt(U^2 + V^2 cos^2 i).
 //   Behind the star (cos phi <= 0, or V <= 0) returns PT_ZBEHIND.
-// *bad is set when Newton did not converge within max_iter steps.
+// Newton stops once the error left after a step, at most (e / (2 (1 - e)))
+// step^2 (|f''| <= e, f' >= 1 - e for this f), is below 3e-8 |dE|: the
+// rounding level of the FP32 evaluation, so no step is spent on merely
+// confirming convergence.  *bad is set when that did not happen within
+// max_iter steps.
+// Warm start: a caller stepping through the supersamples of one exposure
+// passes warm[3] = {dE, dM, dE/dM} of the previous solution (warm[0] NaN for
+// none); the start dE + (dM' - dM) dE/dM is then off by ~e (dM' - dM)^2 / 2,
+// so one Newton step usually converges.  The solution is written back.
 // FAST takes the Newton quotient with __fdividef (its denominator
 // 1 - e cos E lies in [1 - e, 1 + e]) and the final root as x * rsqrtf(x):
-// about one ulp more in z, for the Mandel-Agol kernels.
+// about one ulp more in z.
 template <bool FAST = false>
-__device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_iter, bool *bad)
+__device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_iter, bool *bad, float *warm = nullptr)
 {
     if (r.ecc == 0.0f) {
         float s, c;
@@ -129,22 +137,34 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
         return r.a * (FAST ? fast_sqrt(fmaf(s, s, ci * ci)) : sqrtf(fmaf(s, s, ci * ci)));
     }
     float dM = r.nang * dt;
-    float dE = dM / (1.0f - r.ecE);
-    float sh, ch;
+    float dE = (warm && warm[0] == warm[0]) ? fmaf(dM - warm[1], warm[2], warm[0]) : dM / (1.0f - r.ecE);
+    float sh, ch, dEdM = 1.0f;
     bool conv = false;
     for (int it = 0; it < max_iter; ++it) {
         sincos_near0(0.5f * dE, &sh, &ch);
         float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
         float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
         float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
-        float step = FAST ? __fdividef(F, Fp) : F / Fp;
+        float step;
+        if (FAST) {
+            dEdM = __fdividef(1.0f, Fp);
+            step = F * dEdM;
+        } else {
+            step = F / Fp;
+            if (warm) dEdM = __fdividef(1.0f, Fp);
+        }
         dE -= step;
-        if (fabsf(step) <= 4e-7f * fabsf(dE) + 1e-12f) {
+        if (r.nq * step * step <= 6e-8f * fabsf(dE) + 1e-12f) {
             conv = true;
             break;
         }
     }
     if (!conv) *bad = true;
+    if (warm) {
+        warm[0] = dE;
+        warm[1] = dM;
+        warm[2] = dEdM;
+    }
     sincos_near0(0.5f * dE, &sh, &ch);
     float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
     float dC = -r.cE * omc - r.sE * sn;
@@ -417,7 +437,8 @@ __device__ __forceinline__ void make_geom_rec(double t0, double P, float a_f, fl
     r.Vs = af * swf;
     r.Vc = af * sef * cwf;
     r.Vtr = af * (1.0f - ef * cEf);
-    r.pad0 = r.pad1 = r.pad2 = 0.0f;
+    r.nq = ecc ? (float)(e / (1.0 - e)) : 0.0f;
+    r.pad1 = r.pad2 = 0.0f;
     // Conservative window.  z^2 >= r_min^2 (sin^2(th) sin^2 i + cos^2 i) with
     // th = w + f - pi/2 and r_min = a (1 - e), so z > 1 + k whenever
     // sin^2 th > ((1+k)^2 / r_min^2 - cos^2 i) / sin^2 i.  The true-anomaly

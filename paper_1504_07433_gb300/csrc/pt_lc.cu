@@ -814,7 +814,7 @@ __device__ __forceinline__ void cheb_eval(const float *sd, int nj, const float (
         }
     };
     int m = 2;
-#pragma unroll 1
+#pragma unroll 2
     for (; m + 1 < nj; m += 2) {
         step(m, an, wa, wb);
         step(m + 1, ap, wb, wa);
@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
     extern __shared__ __align__(16) unsigned char dsm[];
     float *sd = reinterpret_cast<float *>(dsm);                  // [n_j][DS] coefficient rows
     float *sS = sd + nj * DS;                                    // [NP1][CH] series values of a chunk
-    float2 *syq = reinterpret_cast<float2 *>(sS + NP1 * CH);     // [GS_THREADS][ssb] (y, q) per pair
+    float2 *syq = reinterpret_cast<float2 *>(sS + NP1 * CH);     // [ssb][GS_THREADS] (y, q) per pair
     __shared__ GeomRec srec;
     __shared__ int sitem, sgeom, sbad;
     __shared__ int sst[GS_THREADS + 1];   // first dense entry of each pair; sst[GS_THREADS] = entries
@@ -890,6 +890,7 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
         float al[NP1];   // alpha sums over the supersamples
 #pragma unroll
         for (int n = 0; n < NP1; ++n) al[n] = 0.0f;
+        float warm[3] = {__int_as_float(0x7fffffff), 0.0f, 0.0f};   // Kepler warm start (none yet)
 #pragma unroll 1
         for (int sb0 = 0; sb0 < nss; sb0 += ssb) {
             // 1. in-transit supersamples of this pair, in order
@@ -899,12 +900,12 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
 #pragma unroll 1
                 for (int s = sb0; s < s1; ++s) {
                     bool bad = false;
-                    const float z = pt::orbit_z(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad);
+                    const float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
                     if (bad) ++nbad;
                     if (z < 1.0f + kk) {
                         const float cz = z / (1.0f + kk);
                         const float x = cz * cz;
-                        syq[tid * ssb + c] = make_float2(fmaf(2.0f, x, -1.0f), sqrtf((1.0f - cz) * (1.0f + cz)));
+                        syq[c * GS_THREADS + tid] = make_float2(fmaf(2.0f, x, -1.0f), sqrtf((1.0f - cz) * (1.0f + cz)));
                         ++c;
                     }
                 }
@@ -948,7 +949,7 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
                         y[u] = 0.0f;
                         if (e < n_e) {
                             while (sst[p + 1] <= e) ++p;
-                            y[u] = syq[p * ssb + (e - sst[p])].x;
+                            y[u] = syq[(e - sst[p]) * GS_THREADS + p].x;
                         }
                     }
                     float2 acc[E][NP1];
@@ -970,7 +971,7 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
                 const int ea = max(my0, c0), eb = min(my0 + c, c0 + CH);
 #pragma unroll 1
                 for (int e = ea; e < eb; ++e) {
-                    const float qu = syq[tid * ssb + (e - my0)].y;
+                    const float qu = syq[(e - my0) * GS_THREADS + tid].y;
                     const float qq = qu * qu;
                     float w = b2 * qq * qq;
 #pragma unroll
@@ -1131,10 +1132,11 @@ __global__ void __launch_bounds__(GS_THREADS) gim_zi_kernel(GimArgs A, const flo
             float dt = pt::reduce_time(ts.x, ts.y, srec);
             const float kk = srec.k;
             const ZiGrid G = zi_grid(kk, n_in, n_edge);
+            float warm[3] = {__int_as_float(0x7fffffff), 0.0f, 0.0f};   // Kepler warm start (none yet)
 #pragma unroll 1
             for (int s = 0; s < nss; ++s) {
                 bool bad = false;
-                float z = pt::orbit_z(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad);
+                float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
                 if (bad) ++nbad;
                 if (!(z < 1.0f + kk)) continue;   // out of transit: alpha = 0
                 int i0;
@@ -1231,10 +1233,11 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
             float2 ts = A.tsplit[t];
             float dt = pt::reduce_time(ts.x, ts.y, srec);
             float le = 0.0f, ld = 0.0f, ed = 0.0f;
+            float warm[3] = {__int_as_float(0x7fffffff), 0.0f, 0.0f};   // Kepler warm start (none yet)
 #pragma unroll 1
             for (int s = 0; s < nss; ++s) {
                 bool bad = false;
-                float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad);
+                float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
                 if (bad) ++nbad;
                 float a0, a1, a2;
                 pt::ma_terms(srec.k, z, &a0, &a1, &a2);
