@@ -343,7 +343,6 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 // ---------------------------------------------------------------------------
 constexpr int GW_VT = 32;         // geometries per CTA of the window kernel (<= 32: one bit each)
 constexpr int GS_THREADS = 128;   // threads per CTA of the evaluation kernels (one pair each)
-constexpr int GS_PAIRS = 2;       // register pairs of supersamples per coefficient load (Chebyshev kernel)
 
 struct GimArgs {
     const float2 *tsplit;
@@ -612,12 +611,6 @@ __global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_ge
     if (threadIdx.x == 0) pref[n_geom] = scarry;
 }
 
-// Two-lane FP32 arithmetic (sm_100 family): __ffma2_rn performs the FMAs of
-// both lanes of a float2 in one instruction, each rounded like fmaf.  The
-// Chebyshev evaluation keeps two supersamples in the two lanes.
-__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-
 // ---------------------------------------------------------------------------
 // Chebyshev form of the series.  For one geometry and order n,
 //   S_n(x) = sum_{j < n_j} T_{n,j} G_j(nu+2, 1; x)
@@ -629,15 +622,14 @@ __device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return 
 // of that degree).  The Chebyshev basis does not depend on n, so one
 // recurrence T_{m+1} = 2y T_m - T_{m-1} per supersample serves all N + 1
 // orders: N + 2 FMAs per term instead of 3 (N + 1).
-// gim_cheb_coef_kernel: one CTA per geometry; node values by the same
-// Clenshaw summation as the series kernel (FP32), then the transform with
+// gim_cheb_coef_kernel: node values by a Clenshaw summation of the Jacobi
+// series (FP32), then the transform with
 // compensated sums (each product and its FMA-exact error added by a two-sum).
 // ---------------------------------------------------------------------------
 // One CTA per (geometry, pair of orders), so that enough warps hide the
 // dependent chains: the node values of the two orders, then their two
 // coefficient rows (one thread per m, cosine table through shared memory).
-// Each coefficient row holds s_m d_{n,m} twice per order (see the evaluation
-// kernel); an order past N (padding of the row) gets zeros.
+// Orders past N (padding of the coefficient rows) get zeros.
 constexpr int CC_CI = 16;   // cosine-table rows per shared-memory chunk
 constexpr int CC_MR = 4;    // coefficient rows per thread: n_j <= CC_MR * 128
 
@@ -735,10 +727,8 @@ __global__ void __launch_bounds__(128) gim_cheb_coef_kernel(const float4 *gtab, 
     for (int r = 0; r < CC_MR; ++r) {
         const int m = threadIdx.x + r * blockDim.x;
         if (m >= n_j) break;
-        const float sg = (m & 2) ? -1.0f : 1.0f;   // s_m: +, +, -, -, ...
-        const float v0 = no > 0 ? sg * (sum[r][0] + err[r][0]) : 0.0f;
-        const float v1 = no > 1 ? sg * (sum[r][1] + err[r][1]) : 0.0f;
-        reinterpret_cast<float4 *>(dtab + ((size_t)g * n_j + m) * DS)[blockIdx.y] = make_float4(v0, v0, v1, v1);
+        float2 o2 = make_float2(no > 0 ? sum[r][0] + err[r][0] : 0.0f, no > 1 ? sum[r][1] + err[r][1] : 0.0f);
+        reinterpret_cast<float2 *>(dtab + ((size_t)g * n_j + m) * DS)[blockIdx.y] = o2;
     }
 }
 
@@ -757,84 +747,119 @@ size_t gim_cheb_coef_smem(int n_j)
 //     the in-transit ones, (y = 2x - 1, q = sqrt(1 - x)) with x = c^2, in
 //     order; a scan over the CTA places every pair's entries in one dense
 //     list (pair-major, supersample-minor);
-//  2. the list is cut into chunks of 2 E GS_THREADS entries; each thread
-//     evaluates 2 E consecutive entries, whatever pairs they belong to, so
-//     that no lane idles on an out-of-transit supersample.  One 64-bit
-//     register holds two entries: one two-lane FMA advances both Chebyshev
-//     recurrences, one two-lane FMA per order n accumulates d_{n,m} T_m for
-//     both (the coefficient rows hold each d_{n,m} twice, one per lane).  The
-//     rows also carry the sign s_m = +1, +1, -1, -1, ... (period 4): with
-//     W_m = s_m T_m the recurrence reads W_{m+1} = (-1)^(m+1) 2y W_m + W_{m-1},
-//     an FMA with no negated operand, and s_m d_{n,m} W_m = d_{n,m} T_m
-//     exactly.  The S_n go to shared memory;
+//  2. the list is cut into rounds; in a round each thread evaluates G
+//     consecutive entries, whatever pairs they belong to, so that no lane
+//     idles on an out-of-transit supersample: one Chebyshev recurrence per
+//     entry, T_{m+1} = 2y T_m - T_{m-1}, and one FMA per order n and m for
+//     d_{n,m} T_m (scalar FMAs: on this part they sustain more FMAs per
+//     cycle than the two-lane form).  Rounds of 8 entries per thread while
+//     the list lasts, then 4, then 2, so that little of the last round is
+//     empty.  The S_n go to shared memory;
 //  3. each thread adds its own pair's b^2 q^(n+4) S_n to alpha_n in
-//     supersample order, so the sums do not depend on the chunking.
+//     supersample order, so the sums do not depend on the rounds.
 // After the last batch, the passband combination of Sec. 2.1.3.
-constexpr int GS_SSB = 16;   // supersamples per batch of the Chebyshev kernel
+constexpr int GS_SSB = 16;    // supersamples per batch of the Chebyshev kernel
+constexpr int GS_GMAX = 4;    // entries per thread in the largest round
 
-template <int NP1, int E>
-__device__ __forceinline__ void cheb_eval(const float *sd, int nj, const float (&y)[2 * E],
-                                          float2 (&acc)[E][NP1])
+template <int NP1, int G>
+__device__ __forceinline__ void cheb_eval(const float *sd, int nj, const float (&y)[G], float (&acc)[G][NP1])
 {
-    constexpr int DS = 4 * ((NP1 + 1) / 2);
-    float2 wa[E], wb[E], ap[E], an[E];
-    {
-        const float2 *d0 = reinterpret_cast<const float2 *>(sd);
-        const float2 *d1 = reinterpret_cast<const float2 *>(sd + DS);
+    constexpr int DS = (NP1 + 3) & ~3;
+    float wa[G], wb[G], a2[G];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float a0 = y[2 * e] + y[2 * e], a1 = y[2 * e + 1] + y[2 * e + 1];
-            ap[e] = make_float2(a0, a1);
-            an[e] = make_float2(-a0, -a1);
-            wa[e] = make_float2(1.0f, 1.0f);
-            wb[e] = make_float2(y[2 * e], y[2 * e + 1]);
+    for (int e = 0; e < G; ++e) {
+        a2[e] = y[e] + y[e];
+        wa[e] = 1.0f;
+        wb[e] = y[e];
 #pragma unroll
-            for (int n = 0; n < NP1; ++n) acc[e][n] = f2_fma(d1[n], wb[e], d0[n]);
-        }
+        for (int n = 0; n < NP1; ++n) acc[e][n] = fmaf(sd[DS + n], wb[e], sd[n]);
     }
-    // one step: W_m from W_{m-1}, W_{m-2}, in place of W_{m-2} (wa for even
-    // m, wb for odd m, so the loop carries no register copies); negative
-    // multiplier for even m
-    auto step = [&](int m, const float2 (&cm)[E], float2 (&wn)[E],
-                    const float2 (&wp)[E]) {
-        float2 dm[NP1];
+    // one step: T_m = 2y T_{m-1} - T_{m-2} in place of T_{m-2} (wa for even m,
+    // wb for odd m, so the loop carries no register copies)
+    auto step = [&](int m, float (&wn)[G], const float (&wp)[G]) {
+        float dm[DS];
         const float4 *row = reinterpret_cast<const float4 *>(sd + m * DS);
 #pragma unroll
-        for (int n = 0; n + 1 < NP1; n += 2) {
-            const float4 v = row[n / 2];
-            dm[n] = make_float2(v.x, v.y);
-            dm[n + 1] = make_float2(v.z, v.w);
+        for (int n = 0; n < DS; n += 4) {
+            const float4 v = row[n / 4];
+            dm[n] = v.x;
+            dm[n + 1] = v.y;
+            dm[n + 2] = v.z;
+            dm[n + 3] = v.w;
         }
-        if (NP1 & 1) dm[NP1 - 1] = reinterpret_cast<const float2 *>(row)[NP1 - 1];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            wn[e] = f2_fma(cm[e], wp[e], wn[e]);
+        for (int e = 0; e < G; ++e) {
+            wn[e] = fmaf(a2[e], wp[e], -wn[e]);
 #pragma unroll
-            for (int n = 0; n < NP1; ++n) acc[e][n] = f2_fma(dm[n], wn[e], acc[e][n]);
+            for (int n = 0; n < NP1; ++n) acc[e][n] = fmaf(dm[n], wn[e], acc[e][n]);
         }
     };
     int m = 2;
 #pragma unroll 2
     for (; m + 1 < nj; m += 2) {
-        step(m, an, wa, wb);
-        step(m + 1, ap, wb, wa);
+        step(m, wa, wb);
+        step(m + 1, wb, wa);
     }
-    if (m < nj) step(m, an, wa, wb);
+    if (m < nj) step(m, wa, wb);
 }
 
-template <int NP1, int E>
+// One round: entries [r0, r0 + G GS_THREADS) of the dense list (those below
+// n_e), G consecutive ones per thread; S_n to sS[n][slot].
+template <int NP1, int G>
+__device__ __forceinline__ void cheb_round(const float *sd, int nj, const float2 *syq, const int *sst, float *sS,
+                                           int r0, int n_e)
+{
+    constexpr int CH = GS_GMAX * GS_THREADS;
+    const int tid = threadIdx.x;
+    const int e0 = r0 + G * tid;
+    if (e0 >= n_e) return;
+    float y[G];
+    int p = 0;
+    {
+        int lo = 0, hi = GS_THREADS - 1;   // the last pair with sst[p] <= e0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sst[mid] <= e0) lo = mid;
+            else hi = mid - 1;
+        }
+        p = lo;
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+        const int e = e0 + u;
+        y[u] = 0.0f;
+        if (e < n_e) {
+            while (sst[p + 1] <= e) ++p;
+            y[u] = syq[(e - sst[p]) * GS_THREADS + p].x;
+        }
+    }
+    float acc[G][NP1];
+    cheb_eval<NP1, G>(sd, nj, y, acc);
+#pragma unroll
+    for (int n = 0; n < NP1; ++n) {
+        float *dst = sS + n * CH + G * tid;
+        if (G % 4 == 0) {
+#pragma unroll
+            for (int u = 0; u < G; u += 4)
+                *reinterpret_cast<float4 *>(dst + u) = make_float4(acc[u][n], acc[u + 1][n], acc[u + 2][n], acc[u + 3][n]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < G; u += 2) *reinterpret_cast<float2 *>(dst + u) = make_float2(acc[u][n], acc[u + 1][n]);
+        }
+    }
+}
+
+template <int NP1>
 __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const float *dtab)
 {
-    constexpr int DS = 4 * ((NP1 + 1) / 2);   // floats per coefficient row
-    constexpr int G = 2 * E;                  // entries per thread and chunk
-    constexpr int CH = G * GS_THREADS;        // entries per chunk
-    static_assert(G == 2 || G == 4, "two or four entries per thread");
+    constexpr int DS = (NP1 + 3) & ~3;        // floats per coefficient row
+    constexpr int CH = GS_GMAX * GS_THREADS;  // entries of the largest round
     const int nj = A.n_j;
     const int nss = A.n_ss;
     const int ssb = min(nss, GS_SSB);
     extern __shared__ __align__(16) unsigned char dsm[];
     float *sd = reinterpret_cast<float *>(dsm);                  // [n_j][DS] coefficient rows
-    float *sS = sd + nj * DS;                                    // [NP1][CH] series values of a chunk
+    float *sS = sd + nj * DS;                                    // [NP1][CH] series values of a round
     float2 *syq = reinterpret_cast<float2 *>(sS + NP1 * CH);     // [ssb][GS_THREADS] (y, q) per pair
     __shared__ GeomRec srec;
     __shared__ int sitem, sgeom, sbad;
@@ -927,48 +952,26 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
             __syncthreads();
             const int n_e = sst[GS_THREADS];
             const int my0 = sst[tid];
+            int r0 = 0;
 #pragma unroll 1
-            for (int c0 = 0; c0 < n_e; c0 += CH) {
-                // 2. series values of G consecutive entries
-                const int e0 = c0 + G * tid;
-                if (e0 < n_e) {
-                    float y[G];
-                    int p = 0;
-                    {
-                        int lo = 0, hi = GS_THREADS - 1;   // the last pair with sst[p] <= e0
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (sst[mid] <= e0) lo = mid;
-                            else hi = mid - 1;
-                        }
-                        p = lo;
-                    }
-#pragma unroll
-                    for (int u = 0; u < G; ++u) {
-                        const int e = e0 + u;
-                        y[u] = 0.0f;
-                        if (e < n_e) {
-                            while (sst[p + 1] <= e) ++p;
-                            y[u] = syq[(e - sst[p]) * GS_THREADS + p].x;
-                        }
-                    }
-                    float2 acc[E][NP1];
-                    cheb_eval<NP1, E>(sd, nj, y, acc);
-#pragma unroll
-                    for (int n = 0; n < NP1; ++n) {
-                        float v[G];
-#pragma unroll
-                        for (int e = 0; e < E; ++e) { v[2 * e] = acc[e][n].x; v[2 * e + 1] = acc[e][n].y; }
-                        if (G == 4)
-                            reinterpret_cast<float4 *>(sS + n * CH)[tid] = make_float4(v[0], v[1], v[2], v[3]);
-                        else
-                            reinterpret_cast<float2 *>(sS + n * CH)[tid] = make_float2(v[0], v[1]);
-                    }
+            while (r0 < n_e) {
+                // 2. a round of series values; its size from what is left
+                const int rem = n_e - r0;
+                int size;
+                if (rem >= GS_GMAX * GS_THREADS) {
+                    cheb_round<NP1, GS_GMAX>(sd, nj, syq, sst, sS, r0, n_e);
+                    size = GS_GMAX * GS_THREADS;
+                } else if (rem >= 4 * GS_THREADS) {
+                    cheb_round<NP1, 4>(sd, nj, syq, sst, sS, r0, n_e);
+                    size = 4 * GS_THREADS;
+                } else {
+                    cheb_round<NP1, 2>(sd, nj, syq, sst, sS, r0, n_e);
+                    size = 2 * GS_THREADS;
                 }
                 __syncthreads();
-                // 3. this pair's entries of the chunk, in supersample order:
+                // 3. this pair's entries of the round, in supersample order:
                 //    alpha_n += b^2 q^(n+4) S_n
-                const int ea = max(my0, c0), eb = min(my0 + c, c0 + CH);
+                const int ea = max(my0, r0), eb = min(my0 + c, r0 + size);
 #pragma unroll 1
                 for (int e = ea; e < eb; ++e) {
                     const float qu = syq[(e - my0) * GS_THREADS + tid].y;
@@ -976,12 +979,13 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
                     float w = b2 * qq * qq;
 #pragma unroll
                     for (int n = 0; n < NP1; n += 2) {
-                        al[n] = fmaf(sS[n * CH + (e - c0)], w, al[n]);
-                        if (n + 1 < NP1) al[n + 1] = fmaf(sS[(n + 1) * CH + (e - c0)], w * qu, al[n + 1]);
+                        al[n] = fmaf(sS[n * CH + (e - r0)], w, al[n]);
+                        if (n + 1 < NP1) al[n + 1] = fmaf(sS[(n + 1) * CH + (e - r0)], w * qu, al[n + 1]);
                         w *= qq;
                     }
                 }
                 __syncthreads();
+                r0 += size;
             }
         }
         if (own) {
@@ -1008,12 +1012,12 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
     if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
 }
 
-// floats per coefficient row: each of the N + 1 orders twice, padded to 16 bytes
-int gim_cheb_ds(int N) { return 4 * ((N + 2) / 2); }
-// coefficient rows, a chunk of series values and a batch of (y, q) entries
+// floats per coefficient row: the N + 1 orders, padded to 16 bytes
+int gim_cheb_ds(int N) { return (N + 4) & ~3; }
+// coefficient rows, a round of series values and a batch of (y, q) entries
 size_t gim_cheb_smem(int n_j, int N, int n_ss)
 {
-    return ((size_t)n_j * gim_cheb_ds(N) + (size_t)(N + 1) * 2 * GS_PAIRS * GS_THREADS) * sizeof(float) +
+    return ((size_t)n_j * gim_cheb_ds(N) + (size_t)(N + 1) * GS_GMAX * GS_THREADS) * sizeof(float) +
            (size_t)GS_THREADS * (n_ss < GS_SSB ? n_ss : GS_SSB) * sizeof(float2);
 }
 
@@ -1492,8 +1496,8 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
         off += align256((size_t)n_v * n_b * n_t * sizeof(float));
         L.atab = off;
         off += align256((size_t)n_geom * n_zi * NP1 * sizeof(float));
-        L.dtab = off;   // Chebyshev coefficient rows: each order twice, padded to 16 bytes
-        off += align256((size_t)n_geom * n_j * (4 * ((NP1 + 1) / 2)) * sizeof(float));
+        L.dtab = off;   // Chebyshev coefficient rows, padded to 16 bytes
+        off += align256((size_t)n_geom * n_j * ((NP1 + 3) & ~3) * sizeof(float));
     }
     L.total = off;
     return L;
@@ -1583,10 +1587,9 @@ template <int NP1>
 int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab,
                   size_t max_items, cudaStream_t s)
 {
-    constexpr int E = GS_PAIRS;
     // coefficients: one CTA per (geometry, pair of orders), every row of
-    // DS floats written (an order past N as zeros)
-    constexpr int DS = 4 * ((NP1 + 1) / 2);
+    // DS floats written (orders past N as zeros)
+    constexpr int DS = (NP1 + 3) & ~3;
     const size_t csm = gim_cheb_coef_smem(A.n_j);
     static thread_local size_t csm_configured = 0;
     if (csm > 48 * 1024 && csm > csm_configured) {
@@ -1595,14 +1598,14 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const floa
         if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_coef_kernel smem attribute");
         csm_configured = csm;
     }
-    gim_cheb_coef_kernel<<<dim3(A.n_geom, DS / 4), 128, csm, s>>>(T, A.N + 1, A.n_j, DS, cx, ccos, dtab);
+    gim_cheb_coef_kernel<<<dim3(A.n_geom, DS / 2), 128, csm, s>>>(T, A.N + 1, A.n_j, DS, cx, ccos, dtab);
     int st = check_launch("gim_cheb_coef_kernel");
     if (st) return st;
     // evaluation: persistent
     const size_t smem = gim_cheb_smem(A.n_j, A.N, A.n_ss);
     static thread_local size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(gim_cheb_kernel<NP1, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(gim_cheb_kernel<NP1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_kernel smem attribute");
         configured = smem;
@@ -1611,13 +1614,13 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const floa
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gim_cheb_kernel<NP1, E>, GS_THREADS, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gim_cheb_kernel<NP1>, GS_THREADS, smem);
     if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_kernel occupancy");
     if (per_sm < 1) return pt_internal::set_error(PT_ERR_ARG, "gim_cheb_kernel", "does not fit on an SM");
     size_t grid = (size_t)n_sm * per_sm;
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
-    gim_cheb_kernel<NP1, E><<<(unsigned)grid, GS_THREADS, smem, s>>>(A, dtab);
+    gim_cheb_kernel<NP1><<<(unsigned)grid, GS_THREADS, smem, s>>>(A, dtab);
     return check_launch("gim_cheb_kernel");
 }
 
