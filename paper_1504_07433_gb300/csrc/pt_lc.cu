@@ -512,14 +512,14 @@ __device__ __forceinline__ void window_cta(const GimArgs &A, int bx, int by)
             }
         }
     }
-    const bool any = __any_sync(0xffffffffu, bits != 0u);
-    if (any) {
-        for (int vl = 0; vl < ng; ++vl) {
-            unsigned mb = __ballot_sync(0xffffffffu, (bits >> vl) & 1u);
-            if (lane == 0) swc[warp][vl] = __popc(mb);
-        }
-    } else if (lane < GW_VT) {
-        swc[warp][lane] = 0;
+    // geometries with a pair in this warp (the ballots below visit only those)
+    const unsigned wbits = __reduce_or_sync(0xffffffffu, bits);
+    if (lane < GW_VT) swc[warp][lane] = 0;
+    __syncwarp();
+    for (unsigned rest = wbits; rest; rest &= rest - 1u) {
+        const int vl = __ffs(rest) - 1;
+        unsigned mb = __ballot_sync(0xffffffffu, (bits >> vl) & 1u);
+        if (lane == 0) swc[warp][vl] = __popc(mb);
     }
     __syncthreads();
     if (tl < ng) {   // per geometry: warp offsets, then one reservation
@@ -532,9 +532,10 @@ __device__ __forceinline__ void window_cta(const GimArgs &A, int bx, int by)
         sbase[tl] = run > 0 ? atomicAdd(A.cnt + g0 + tl, run) : 0;
     }
     __syncthreads();
-    if (any) {
+    {
         const unsigned lt = (1u << lane) - 1u;
-        for (int vl = 0; vl < ng; ++vl) {
+        for (unsigned rest = wbits; rest; rest &= rest - 1u) {
+            const int vl = __ffs(rest) - 1;
             const bool in = (bits >> vl) & 1u;
             unsigned mb = __ballot_sync(0xffffffffu, in);
             if (in) A.list[(size_t)(g0 + vl) * A.n_t + sbase[vl] + swc[warp][vl] + __popc(mb & lt)] = t;
@@ -1188,18 +1189,38 @@ size_t gim_zi_smem(int N, int nz) { return (size_t)(N + 1) * (nz + GS_THREADS) *
 
 // ---------------------------------------------------------------------------
 // Mandel-Agol over the window kernel's pair lists: persistent CTAs take work
-// items of MA_PPI listed (time, geometry) pairs; each thread evaluates its
-// pair's supersamples (z, then lambda_e, lambda_d + 2/3 Theta, eta_d), sums
-// them in order and writes every passband's flux (Eq. ma_model).
+// items of MA_PPI listed (time, geometry) pairs.  An item runs in batches of
+// up to MA_SSB supersamples:
+//  1. each thread (one pair) computes z at the batch's supersamples and keeps
+//     the in-transit ones (z < 1 + k) in order; a scan over the CTA places
+//     every pair's z in one dense list (pair-major, supersample-minor);
+//  2. rounds of MA_G MA_PPI entries: each thread evaluates lambda_e,
+//     lambda_d + 2/3 Theta and eta_d at MA_G entries (strided, so that a warp
+//     takes consecutive entries), whatever pairs they belong to, so that no
+//     lane idles on an out-of-transit supersample; the terms go to shared
+//     memory;
+//  3. each thread adds its own pair's terms in supersample order (the others
+//     are zero), so the sums do not depend on the rounds.
+// Then the passband fluxes (Eq. ma_model).
 // ---------------------------------------------------------------------------
-constexpr int MA_PPI = 64;   // pairs per work item (= threads per CTA)
+constexpr int MA_PPI = 128;   // pairs per work item (= threads per CTA)
+constexpr int MA_SSB = 16;    // supersamples per batch
+constexpr int MA_G = 4;       // entries per thread and round
 
 __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
 {
+    constexpr int CH = MA_G * MA_PPI;   // entries per round
     __shared__ GeomRec srec;
     __shared__ int sitem, sgeom, sbad;
+    __shared__ int sst[MA_PPI + 1];      // first dense entry of each pair; sst[MA_PPI] = entries
+    __shared__ int swarp[MA_PPI / 32];
+    __shared__ float szp[MA_SSB * MA_PPI];   // [c][pair] in-transit z of each pair, in order
+    __shared__ float sz[MA_SSB * MA_PPI];    // the dense list
+    __shared__ float sT[3][CH];              // terms of a round
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int nss = A.n_ss;
+    const int ssb = min(nss, MA_SSB);
     const int total = A.pref[A.n_geom];
     const float inv_nss = 1.0f / (float)nss;
     int nbad = 0;
@@ -1232,23 +1253,74 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
         }
         __syncthreads();
         const int i = (it - A.pref[g]) * MA_PPI + tid;
-        if (i < A.cnt[g]) {
-            const int t = A.list[(size_t)g * A.n_t + i];
-            float2 ts = A.tsplit[t];
-            float dt = pt::reduce_time(ts.x, ts.y, srec);
-            float le = 0.0f, ld = 0.0f, ed = 0.0f;
-            float warm[3] = {__int_as_float(0x7fffffff), 0.0f, 0.0f};   // Kepler warm start (none yet)
+        const bool own = i < A.cnt[g];
+        const int t = own ? A.list[(size_t)g * A.n_t + i] : 0;
+        float dt = 0.0f;
+        if (own) {
+            const float2 ts = A.tsplit[t];
+            dt = pt::reduce_time(ts.x, ts.y, srec);
+        }
+        const float kk = srec.k;
+        float le = 0.0f, ld = 0.0f, ed = 0.0f;
+        float warm[3] = {__int_as_float(0x7fffffff), 0.0f, 0.0f};   // Kepler warm start (none yet)
 #pragma unroll 1
-            for (int s = 0; s < nss; ++s) {
-                bool bad = false;
-                float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
-                if (bad) ++nbad;
-                float a0, a1, a2;
-                pt::ma_terms(srec.k, z, &a0, &a1, &a2);
-                le += a0;
-                ld += a1;
-                ed += a2;
+        for (int sb0 = 0; sb0 < nss; sb0 += ssb) {
+            // 1. in-transit supersamples of this pair, in order (the terms of
+            //    the others are zero: ma_terms returns zeros there)
+            int c = 0;
+            if (own) {
+                const int s1 = min(nss, sb0 + ssb);
+#pragma unroll 1
+                for (int s = sb0; s < s1; ++s) {
+                    bool bad = false;
+                    const float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
+                    if (bad) ++nbad;
+                    if (z < 1.0f + kk && kk > 0.0f) szp[(c++) * MA_PPI + tid] = z;
+                }
             }
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) swarp[warp] = incl;
+            __syncthreads();
+            int base = 0;
+#pragma unroll
+            for (int w = 0; w < MA_PPI / 32; ++w) base += (w < warp) ? swarp[w] : 0;
+            const int my0 = base + incl - c;
+            for (int j = 0; j < c; ++j) sz[my0 + j] = szp[j * MA_PPI + tid];
+            if (tid == MA_PPI - 1) sst[MA_PPI] = base + incl;
+            __syncthreads();
+            const int n_e = sst[MA_PPI];
+#pragma unroll 1
+            for (int r0 = 0; r0 < n_e; r0 += CH) {
+                // 2. the terms of a round of entries
+#pragma unroll 1
+                for (int u = 0; u < MA_G; ++u) {
+                    const int e = r0 + u * MA_PPI + tid;
+                    if (e < n_e) {
+                        float a0, a1, a2;
+                        pt::ma_terms(kk, sz[e], &a0, &a1, &a2);
+                        sT[0][e - r0] = a0;
+                        sT[1][e - r0] = a1;
+                        sT[2][e - r0] = a2;
+                    }
+                }
+                __syncthreads();
+                // 3. this pair's entries of the round, in supersample order
+                const int ea = max(my0, r0), eb = min(my0 + c, r0 + CH);
+#pragma unroll 1
+                for (int e = ea; e < eb; ++e) {
+                    le += sT[0][e - r0];
+                    ld += sT[1][e - r0];
+                    ed += sT[2][e - r0];
+                }
+                __syncthreads();
+            }
+        }
+        if (own) {
             le *= inv_nss;
             ld *= inv_nss;
             ed *= inv_nss;
