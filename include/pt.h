@@ -391,6 +391,15 @@ typedef struct pt_gim_plan_s *pt_gim_plan;
 int pt_gim_plan_create(int N, int n_j, pt_gim_plan *plan_out);
 int pt_gim_plan_destroy(pt_gim_plan plan);
 
+/* Profiling hook: ev_start and ev_end (cudaEvent_t handles, owned by the
+ * caller, which keeps them alive while calls use them) are recorded on the
+ * call's stream right before and right after the series-evaluation kernel
+ * of every later pt_gimenez call with this plan, so that the caller can time
+ * that kernel alone; NULL, NULL stops it.  This is the one setting that
+ * changes a plan: a plan with events set must not be used by two host
+ * threads at once.  PT_ERR_ARG for a NULL plan or exactly one NULL event. */
+int pt_gim_plan_time_evaluation(pt_gim_plan plan, void *ev_start, void *ev_end);
+
 /* Pointwise alpha_n (Eq. gimenez): alpha_dev is [n][N+1] for n pairs (k, z). */
 int pt_gimenez_alpha(pt_gim_plan plan, const float *k_dev, const float *z_dev, size_t n,
                      float *alpha_dev, pt_stream_t stream);

@@ -83,6 +83,7 @@ def load_library(build_if_missing: bool = False):
                                        _c_double, _c_int, P, P, P, P, P, _c_size, P, P]),
         "pt_gim_plan_create": (_c_int, [_c_int, _c_int, ctypes.POINTER(_c_void_p)]),
         "pt_gim_plan_destroy": (_c_int, [P]),
+        "pt_gim_plan_time_evaluation": (_c_int, [P, P, P]),
         "pt_gimenez_alpha": (_c_int, [P, P, P, _c_size, P, P]),
         "pt_gimenez_work_bytes": (_c_size, [P, _c_int, _c_int, _c_int, _c_int]),
         "pt_gimenez": (_c_int, [P, P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int, _c_double,
@@ -315,6 +316,21 @@ class GimenezPlan:
 
     def work_bytes(self, n_t, n_v, n_b, k_per_band=False):
         return int(load_library().pt_gimenez_work_bytes(self.handle, n_t, n_v, n_b, int(bool(k_per_band))))
+
+    def time_evaluation(self, start=None, end=None):
+        """Record the torch.cuda.Event pair start/end around the series
+        evaluation kernel of later gimenez() calls with this plan
+        (pt_gim_plan_time_evaluation); no arguments stops it."""
+        h0 = h1 = None
+        if start is not None or end is not None:
+            if start is None or end is None:
+                raise PTError("time_evaluation needs both events or neither")
+            for e in (start, end):
+                if not e.cuda_event:   # the CUDA event is created on its first record
+                    e.record()
+            h0, h1 = _c_void_p(start.cuda_event), _c_void_p(end.cuda_event)
+        _check(load_library().pt_gim_plan_time_evaluation(self.handle, h0, h1), "pt_gim_plan_time_evaluation")
+        self._timing_events = (start, end)   # kept alive while the plan records them
 
 
 def gimenez_alpha(plan, k, z):

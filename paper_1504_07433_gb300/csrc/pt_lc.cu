@@ -1600,6 +1600,7 @@ struct pt_gim_plan_s {
     double *d_recb;   // [N+1][n_j][3]: recursion of G_j(nu+2, nu+1; x), FP64
     float *d_cx;      // [n_j]: Chebyshev nodes in x, (1 + cos(pi (i + 1/2) / n_j)) / 2
     float *d_ccos;    // [n_j (i)][n_j (m)]: (2 / n_j) cos(pi m (i + 1/2) / n_j), column m = 0 halved
+    cudaEvent_t ev0, ev1;   // recorded around the series evaluation kernel when set (profiling)
 };
 
 namespace {
@@ -1657,7 +1658,7 @@ int launch_zi(const GimArgs &A, const float *atab, int n_in, int n_edge, size_t 
 
 template <int NP1>
 int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab,
-                  size_t max_items, cudaStream_t s)
+                  size_t max_items, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s)
 {
     // coefficients: one CTA per (geometry, pair of orders), every row of
     // DS floats written (orders past N as zeros)
@@ -1692,31 +1693,35 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const floa
     size_t grid = (size_t)n_sm * per_sm;
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
+    if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return set_cuda_error(e, "pt_gimenez timing event");
     gim_cheb_kernel<NP1><<<(unsigned)grid, GS_THREADS, smem, s>>>(A, dtab);
-    return check_launch("gim_cheb_kernel");
+    st = check_launch("gim_cheb_kernel");
+    if (st) return st;
+    if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return set_cuda_error(e, "pt_gimenez timing event");
+    return PT_OK;
 }
 
 // Chebyshev path: coefficient and evaluation kernels, for N + 1 orders.
 int launch_cheb(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab, size_t max_items,
-                cudaStream_t s)
+                cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s)
 {
     switch (A.N + 1) {
-    case 2: return launch_cheb_t<2>(A, T, cx, ccos, dtab, max_items, s);
-    case 3: return launch_cheb_t<3>(A, T, cx, ccos, dtab, max_items, s);
-    case 4: return launch_cheb_t<4>(A, T, cx, ccos, dtab, max_items, s);
-    case 5: return launch_cheb_t<5>(A, T, cx, ccos, dtab, max_items, s);
-    case 6: return launch_cheb_t<6>(A, T, cx, ccos, dtab, max_items, s);
-    case 7: return launch_cheb_t<7>(A, T, cx, ccos, dtab, max_items, s);
-    case 8: return launch_cheb_t<8>(A, T, cx, ccos, dtab, max_items, s);
-    case 9: return launch_cheb_t<9>(A, T, cx, ccos, dtab, max_items, s);
-    case 10: return launch_cheb_t<10>(A, T, cx, ccos, dtab, max_items, s);
-    case 11: return launch_cheb_t<11>(A, T, cx, ccos, dtab, max_items, s);
-    case 12: return launch_cheb_t<12>(A, T, cx, ccos, dtab, max_items, s);
-    case 13: return launch_cheb_t<13>(A, T, cx, ccos, dtab, max_items, s);
-    case 14: return launch_cheb_t<14>(A, T, cx, ccos, dtab, max_items, s);
-    case 15: return launch_cheb_t<15>(A, T, cx, ccos, dtab, max_items, s);
-    case 16: return launch_cheb_t<16>(A, T, cx, ccos, dtab, max_items, s);
-    default: return launch_cheb_t<17>(A, T, cx, ccos, dtab, max_items, s);
+    case 2: return launch_cheb_t<2>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 3: return launch_cheb_t<3>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 4: return launch_cheb_t<4>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 5: return launch_cheb_t<5>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 6: return launch_cheb_t<6>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 7: return launch_cheb_t<7>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 8: return launch_cheb_t<8>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 9: return launch_cheb_t<9>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 10: return launch_cheb_t<10>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 11: return launch_cheb_t<11>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 12: return launch_cheb_t<12>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 13: return launch_cheb_t<13>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 14: return launch_cheb_t<14>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 15: return launch_cheb_t<15>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 16: return launch_cheb_t<16>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    default: return launch_cheb_t<17>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
     }
 }
 
@@ -2083,6 +2088,7 @@ int pt_gim_plan_create(int N, int n_j, pt_gim_plan *out)
     p->d_recb = nullptr;
     p->d_cx = nullptr;
     p->d_ccos = nullptr;
+    p->ev0 = p->ev1 = nullptr;
     cudaError_t e = cudaMalloc(&p->d_coef, cnt * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_A, cnt * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_recb, cnt * 3 * sizeof(double));
@@ -2109,6 +2115,14 @@ int pt_gim_plan_create(int N, int n_j, pt_gim_plan *out)
         return set_cuda_error(e, "pt_gim_plan_create");
     }
     *out = p;
+    return PT_OK;
+}
+
+int pt_gim_plan_time_evaluation(pt_gim_plan p, void *ev_start, void *ev_end)
+{
+    if (!p || (ev_start == nullptr) != (ev_end == nullptr)) return PT_ERR_ARG;
+    p->ev0 = (cudaEvent_t)ev_start;
+    p->ev1 = (cudaEvent_t)ev_end;
     return PT_OK;
 }
 
@@ -2237,7 +2251,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     if (zi)
         st = launch_zi(A, atab, n_in, n_edge, smem, max_items, s);
     else
-        st = launch_cheb(A, T, plan->d_cx, plan->d_ccos, dtab, max_items, s);
+        st = launch_cheb(A, T, plan->d_cx, plan->d_ccos, dtab, max_items, plan->ev0, plan->ev1, s);
     if (st) return st;
     if (ssr) {
         ssr_rows_kernel<<<orb->n_v * n_b, 256, 0, s>>>(A.flux, y, wt, n_t, n_b, ssr);

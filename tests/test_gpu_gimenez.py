@@ -216,3 +216,31 @@ def test_gimenez_series_depths(torch_cuda, N, n_j):
     ref = _oracle_lc(wl, n_j)
     assert (ref < 1).sum() > 0
     assert np.max(np.abs(flux.cpu().numpy() - ref)) <= TOL
+
+
+def test_evaluation_timing_events(torch_cuda):
+    """pt_gim_plan_time_evaluation records the caller's events around the
+    series-evaluation kernel only: inside the call's own time, results
+    unchanged, and switched off again by passing no events."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=16, n_t=20000)
+    wl["ld"] = wl["ld_gim"]
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(8, 128)
+    f0, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.time_evaluation(e0, e1)
+    c0.record()
+    f1, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+    c1.record()
+    torch.cuda.synchronize()
+    kernel_ms, call_ms = e0.elapsed_time(e1), c0.elapsed_time(c1)
+    assert 0.0 < kernel_ms < call_ms
+    assert torch.equal(f0, f1)
+    plan.time_evaluation()
+    f2, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+    assert torch.equal(f0, f2)
+    with pytest.raises(pt.PTError):
+        plan.time_evaluation(e0, None)
