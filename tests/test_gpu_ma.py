@@ -124,7 +124,9 @@ def test_ma_quad_plain(torch_cuda):
     assert f.min() < 0.99
 
 
-@pytest.mark.parametrize("n_t,n_v,n_ss,n_b", [(3001, 21, 10, 2), (257, 9, 3, 1), (1, 1, 1, 1), (255, 8, 7, 3)])
+# n_ss = 37 runs the pairs kernel in three batches of supersamples (16, 16, 5)
+@pytest.mark.parametrize("n_t,n_v,n_ss,n_b", [(3001, 21, 10, 2), (257, 9, 3, 1), (1, 1, 1, 1), (255, 8, 7, 3),
+                                              (600, 4, 37, 2)])
 def test_ma_quad_eccentric_supersampled(torch_cuda, n_t, n_v, n_ss, n_b):
     import paper_1504_07433_gb300 as pt
     torch = torch_cuda
