@@ -1193,34 +1193,36 @@ size_t gim_zi_smem(int N, int nz) { return (size_t)(N + 1) * (nz + GS_THREADS) *
 // up to MA_SSB supersamples:
 //  1. each thread (one pair) computes z at the batch's supersamples and keeps
 //     the in-transit ones (z < 1 + k) in order; a scan over the CTA places
-//     every pair's z in one dense list (pair-major, supersample-minor);
-//  2. rounds of MA_G MA_PPI entries: each thread evaluates lambda_e,
-//     lambda_d + 2/3 Theta and eta_d at MA_G entries (strided, so that a warp
-//     takes consecutive entries), whatever pairs they belong to, so that no
-//     lane idles on an out-of-transit supersample; the terms go to shared
-//     memory;
+//     every pair's z in one dense list, the supersamples with the planet
+//     wholly inside the stellar disk (z <= 1 - k) first and those on the limb
+//     after them, and records where each of its entries went;
+//  2. each thread evaluates lambda_e, lambda_d + 2/3 Theta and eta_d at
+//     entries tid, tid + MA_PPI, ... of the list, whatever pairs they belong
+//     to: no lane idles on an out-of-transit supersample, and a warp mostly
+//     takes one branch of the case table (the limb cases add the lens
+//     geometry).  The terms go to shared memory;
 //  3. each thread adds its own pair's terms in supersample order (the others
-//     are zero), so the sums do not depend on the rounds.
+//     are zero), so the sums do not depend on where the terms were computed.
 // Then the passband fluxes (Eq. ma_model).
 // ---------------------------------------------------------------------------
 constexpr int MA_PPI = 128;   // pairs per work item (= threads per CTA)
 constexpr int MA_SSB = 16;    // supersamples per batch
-constexpr int MA_G = 4;       // entries per thread and round
 
 __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
 {
-    constexpr int CH = MA_G * MA_PPI;   // entries per round
     __shared__ GeomRec srec;
     __shared__ int sitem, sgeom, sbad;
-    __shared__ int sst[MA_PPI + 1];      // first dense entry of each pair; sst[MA_PPI] = entries
+    __shared__ int sn[2];                    // entries inside, entries on the limb
     __shared__ int swarp[MA_PPI / 32];
-    __shared__ float szp[MA_SSB * MA_PPI];   // [c][pair] in-transit z of each pair, in order
-    __shared__ float sz[MA_SSB * MA_PPI];    // the dense list
-    __shared__ float sT[3][CH];              // terms of a round
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int nss = A.n_ss;
     const int ssb = min(nss, MA_SSB);
+    extern __shared__ __align__(16) unsigned char msm[];
+    float *sT = reinterpret_cast<float *>(msm);                     // [3][ssb MA_PPI] terms of the list
+    float *sz = sT + 3 * ssb * MA_PPI;                              // [ssb MA_PPI] the dense list of z
+    float *szp = sz + ssb * MA_PPI;                                 // [ssb][MA_PPI] each pair's z, in order
+    unsigned short *spos = reinterpret_cast<unsigned short *>(szp + ssb * MA_PPI);   // [ssb][MA_PPI] list slots
     const int total = A.pref[A.n_geom];
     const float inv_nss = 1.0f / (float)nss;
     int nbad = 0;
@@ -1266,8 +1268,10 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
 #pragma unroll 1
         for (int sb0 = 0; sb0 < nss; sb0 += ssb) {
             // 1. in-transit supersamples of this pair, in order (the terms of
-            //    the others are zero: ma_terms returns zeros there)
-            int c = 0;
+            //    the others are zero: ma_terms returns zeros there), and which
+            //    of them have the planet wholly inside the disk
+            int c = 0, n_in = 0;
+            unsigned limb = 0u;
             if (own) {
                 const int s1 = min(nss, sb0 + ssb);
 #pragma unroll 1
@@ -1275,50 +1279,60 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
                     bool bad = false;
                     const float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
                     if (bad) ++nbad;
-                    if (z < 1.0f + kk && kk > 0.0f) szp[(c++) * MA_PPI + tid] = z;
+                    if (z < 1.0f + kk && kk > 0.0f) {
+                        szp[c * MA_PPI + tid] = z;
+                        if ((z - 1.0f) + kk > 0.0f) limb |= 1u << c;
+                        else ++n_in;
+                        ++c;
+                    }
                 }
             }
-            int incl = c;
+            // both classes' counts in one scan: inside in the low 16 bits,
+            // limb in the high ones (at most MA_SSB MA_PPI = 2048 each)
+            const int v = n_in | ((c - n_in) << 16);
+            int incl = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
             if (lane == 31) swarp[warp] = incl;
             __syncthreads();
-            int base = 0;
+            int base = 0, all = 0;
 #pragma unroll
-            for (int w = 0; w < MA_PPI / 32; ++w) base += (w < warp) ? swarp[w] : 0;
-            const int my0 = base + incl - c;
-            for (int j = 0; j < c; ++j) sz[my0 + j] = szp[j * MA_PPI + tid];
-            if (tid == MA_PPI - 1) sst[MA_PPI] = base + incl;
-            __syncthreads();
-            const int n_e = sst[MA_PPI];
-#pragma unroll 1
-            for (int r0 = 0; r0 < n_e; r0 += CH) {
-                // 2. the terms of a round of entries
-#pragma unroll 1
-                for (int u = 0; u < MA_G; ++u) {
-                    const int e = r0 + u * MA_PPI + tid;
-                    if (e < n_e) {
-                        float a0, a1, a2;
-                        pt::ma_terms(kk, sz[e], &a0, &a1, &a2);
-                        sT[0][e - r0] = a0;
-                        sT[1][e - r0] = a1;
-                        sT[2][e - r0] = a2;
-                    }
-                }
-                __syncthreads();
-                // 3. this pair's entries of the round, in supersample order
-                const int ea = max(my0, r0), eb = min(my0 + c, r0 + CH);
-#pragma unroll 1
-                for (int e = ea; e < eb; ++e) {
-                    le += sT[0][e - r0];
-                    ld += sT[1][e - r0];
-                    ed += sT[2][e - r0];
-                }
-                __syncthreads();
+            for (int w = 0; w < MA_PPI / 32; ++w) {
+                base += (w < warp) ? swarp[w] : 0;
+                all += swarp[w];
             }
+            const int excl = base + incl - v;
+            const int n_inside = all & 0xffff;
+            int p_in = excl & 0xffff, p_limb = n_inside + (excl >> 16);
+            for (int j = 0; j < c; ++j) {
+                const int pos = ((limb >> j) & 1u) ? p_limb++ : p_in++;
+                sz[pos] = szp[j * MA_PPI + tid];
+                spos[j * MA_PPI + tid] = (unsigned short)pos;
+            }
+            const int n_e = n_inside + (all >> 16);
+            __syncthreads();
+            // 2. the terms of every entry of the list
+            const int stride = ssb * MA_PPI;
+#pragma unroll 1
+            for (int e = tid; e < n_e; e += MA_PPI) {
+                float a0, a1, a2;
+                pt::ma_terms(kk, sz[e], &a0, &a1, &a2);
+                sT[e] = a0;
+                sT[stride + e] = a1;
+                sT[2 * stride + e] = a2;
+            }
+            __syncthreads();
+            // 3. this pair's terms, in supersample order
+            for (int j = 0; j < c; ++j) {
+                const int pos = spos[j * MA_PPI + tid];
+                le += sT[pos];
+                ld += sT[stride + pos];
+                ed += sT[2 * stride + pos];
+            }
+            __syncthreads();
         }
         if (own) {
             le *= inv_nss;
@@ -1336,6 +1350,13 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
     if (nbad) atomicAdd(&sbad, nbad);
     __syncthreads();
     if (tid == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
+}
+
+// the list's terms, the list, each pair's z and the list slots
+size_t ma_pairs_smem(int n_ss)
+{
+    const size_t n = (size_t)(n_ss < MA_SSB ? n_ss : MA_SSB) * MA_PPI;
+    return n * (5 * sizeof(float) + sizeof(unsigned short));
 }
 
 __global__ void ssr_reduce_kernel(const float *part, int rows, int n_tiles, float *ssr)
@@ -1893,16 +1914,17 @@ static int ma_quad_list(const double *t, int n_t, const pt_orbit *orb, const flo
     gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, MA_PPI, A.pref, A.ctr);
     st = check_launch("gim_scan_kernel");
     if (st) return st;
+    const size_t msm = ma_pairs_smem(n_ss);   // at most 44 KB: no opt-in needed
     int dev = 0, n_sm = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ma_pairs_kernel, MA_PPI, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ma_pairs_kernel, MA_PPI, msm);
     if (e != cudaSuccess) return set_cuda_error(e, "ma_pairs_kernel occupancy");
     size_t grid = (size_t)n_sm * (per_sm > 0 ? per_sm : 1);
     const size_t max_items = (size_t)n_geom * ((n_t + MA_PPI - 1) / MA_PPI);
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
-    ma_pairs_kernel<<<(unsigned)grid, MA_PPI, 0, s>>>(A);
+    ma_pairs_kernel<<<(unsigned)grid, MA_PPI, msm, s>>>(A);
     st = check_launch("ma_pairs_kernel");
     if (st) return st;
     if (ssr) {
