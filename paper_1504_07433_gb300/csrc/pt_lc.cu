@@ -361,7 +361,7 @@ struct GimArgs {
     int *pref;            // [n_geom + 1] work items before each geometry
     int *ctr;             // next work item of the series kernel
     int *list;            // [n_geom][n_t] time indices of listed pairs
-    int ppi;              // pairs per work item (GS_THREADS or GS_THREADS / 2)
+    int ppi;              // pairs per work item (GS_THREADS or MA_PPI)
     int *n_bad;
 };
 
