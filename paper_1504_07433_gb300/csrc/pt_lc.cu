@@ -501,15 +501,20 @@ __device__ __forceinline__ void window_cta(const GimArgs &A, int bx, int by)
     unsigned bits = 0u;
     if (tv) {
         const float th = ts.x;
+        // first pass without branches: a mask of the candidates ...
+        unsigned cand = 0u;
 #pragma unroll 8
         for (int vl = 0; vl < ng; ++vl) {
-            float4 q = stest[vl];
-            float sv = th - q.x;
-            float d = fmaf(-rintf(sv * q.y), q.z, sv);
-            if (d >= q.w && d <= shi[vl]) {   // candidate: the exact test
-                float dt = pt::reduce_time(th, ts.y, srec[vl]);
-                if ((dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi)) bits |= 1u << vl;
-            }
+            const float4 q = stest[vl];
+            const float sv = th - q.x;
+            const float d = fmaf(-rintf(sv * q.y), q.z, sv);
+            cand |= ((d >= q.w) & (d <= shi[vl])) ? (1u << vl) : 0u;
+        }
+        // ... then the exact test for those only
+        for (unsigned rest = cand; rest; rest &= rest - 1u) {
+            const int vl = __ffs(rest) - 1;
+            const float dt = pt::reduce_time(th, ts.y, srec[vl]);
+            if ((dt >= srec[vl].win_lo) && (dt <= srec[vl].win_hi)) bits |= 1u << vl;
         }
     }
     // geometries with a pair in this warp (the ballots below visit only those)
