@@ -66,7 +66,10 @@ def test_noalloc_matches_work_buffer_entry_point_twice(env):
     f_ref, s_ref = pt.ma_quad(t, orb, k, ld, n_ss=10, t_exp=wl["t_exp"], y=y, want_ssr=True)
     assert (f_ref < 1).sum().item() > 0
     assert torch.max(torch.abs(f_na - f_ref)).item() <= TOL
-    assert torch.allclose(s_na, s_ref, rtol=1e-5, atol=0)
+    # the residual sums agree to what the flux tolerance implies:
+    # |sum (y - f1)^2 - sum (y - f2)^2| <= sum (2 |y - f| TOL + TOL^2)
+    bound = (2.0 * TOL * torch.abs(y[None] - f_ref).double().sum(dim=2) + t.numel() * TOL ** 2)
+    assert torch.all(torch.abs(s_na.double() - s_ref.double()) <= bound)
     # call 2, straight after: a different, smaller circular problem with per-band k
     wl2 = W.batched(n_walkers=7, n_pb=3, n_lc=2, len_lo=300, len_hi=600)
     t2, orb2, k2, ld2 = gpu_inputs(wl2)
