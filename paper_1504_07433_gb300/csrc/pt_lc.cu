@@ -758,9 +758,10 @@ size_t gim_cheb_coef_smem(int n_j)
 //     idles on an out-of-transit supersample: one Chebyshev recurrence per
 //     entry, T_{m+1} = 2y T_m - T_{m-1}, and one FMA per order n and m for
 //     d_{n,m} T_m (scalar FMAs: on this part they sustain more FMAs per
-//     cycle than the two-lane form).  Rounds of 8 entries per thread while
-//     the list lasts, then 4, then 2, so that little of the last round is
-//     empty.  The S_n go to shared memory;
+//     cycle than the two-lane form).  Rounds of GS_GMAX = 4 entries per
+//     thread while at least 4 GS_THREADS entries are left, then rounds of 2
+//     (each coefficient load serves the thread's entries; smaller rounds
+//     leave less of the last one empty).  The S_n go to shared memory;
 //  3. each thread adds its own pair's b^2 q^(n+4) S_n to alpha_n in
 //     supersample order, so the sums do not depend on the rounds.
 // After the last batch, the passband combination of Sec. 2.1.3.
@@ -967,9 +968,6 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
                 if (rem >= GS_GMAX * GS_THREADS) {
                     cheb_round<NP1, GS_GMAX>(sd, nj, syq, sst, sS, r0, n_e);
                     size = GS_GMAX * GS_THREADS;
-                } else if (rem >= 4 * GS_THREADS) {
-                    cheb_round<NP1, 4>(sd, nj, syq, sst, sS, r0, n_e);
-                    size = 4 * GS_THREADS;
                 } else {
                     cheb_round<NP1, 2>(sd, nj, syq, sst, sS, r0, n_e);
                     size = 2 * GS_THREADS;
