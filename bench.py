@@ -103,6 +103,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def whole_job_rate(ms_local, pts_per_rank, ws, device="cpu"):
+    """The job's time per step is the slowest rank's (a MAX all-reduce when
+    ws > 1); the rate counts the points of every rank (weak scaling: each
+    rank evaluates its own replica).  Returns (ms, points/s)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, pts_per_rank * ws / (ms * 1e-3)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -558,12 +571,8 @@ def main():
     ma_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
     g_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
     k_ms = [evk[i][0].elapsed_time(evk[i][1]) for i in range(K)]
-    tmax = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    step_ms = float(tmax.item())
     pts_per_step = 2 * n_t * n_v * 1
-    value = pts_per_step * ws / (step_ms * 1e-3)
+    step_ms, value = whole_job_rate(step_ms, pts_per_step, ws, dev)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -636,11 +645,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1) / K
-        em = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        if ws > 1:
-            dist.all_reduce(em, op=dist.ReduceOp.MAX)
-        e2e = {"value": pts_per_step * ws / (float(em.item()) * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": float(em.item())}
+        e_ms, e_value = whole_job_rate(e_ms, pts_per_step, ws, dev)
+        e2e = {"value": e_value, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms}
 
     # roofline of the dominant kernel (the Gimenez series evaluation):
     # algorithmic work = evaluating the N + 1 truncated series at each
