@@ -138,14 +138,13 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
     }
     float dM = r.nang * dt;
     float dE = (warm && warm[0] == warm[0]) ? fmaf(dM - warm[1], warm[2], warm[0]) : dM / (1.0f - r.ecE);
-    float sh, ch, dEdM = 1.0f;
+    float sh = 0.0f, ch = 1.0f, dEdM = 1.0f, step = 0.0f;
     bool conv = false;
     for (int it = 0; it < max_iter; ++it) {
         sincos_near0(0.5f * dE, &sh, &ch);
         float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
         float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
         float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
-        float step;
         if (FAST) {
             dEdM = __fdividef(1.0f, Fp);
             step = F * dEdM;
@@ -165,7 +164,19 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
         warm[1] = dM;
         warm[2] = dEdM;
     }
-    sincos_near0(0.5f * dE, &sh, &ch);
+    // sin and cos of dE/2 at the solution: the last step's values rotated by
+    // -step/2 with cos(step/2) ~ 1 - step^2/8, sin(step/2) ~ step/2, instead
+    // of a new series.  The dropped terms are third order in step/2: the
+    // stopping rule accepts |step| <= sqrt(6e-8 |dE| / nq) (< 1e-3 unless e
+    // is tiny, where the Newton step itself is at most e |dM|), so they stay
+    // below 1e-10.
+    {
+        const float h = 0.5f * step;
+        const float c = fmaf(-0.5f * h, h, 1.0f);
+        const float sh1 = fmaf(-ch, h, sh * c);
+        ch = fmaf(sh, h, ch * c);
+        sh = sh1;
+    }
     float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
     float dC = -r.cE * omc - r.sE * sn;
     float dS = r.cE * sn - r.sE * omc;
