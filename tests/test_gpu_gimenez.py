@@ -75,9 +75,9 @@ def test_gimenez_lc_vs_oracle(torch_cuda, n_t, n_v, n_ss, n_j):
 
 @pytest.mark.parametrize("N,n_ss", [(1, 4), (3, 7), (16, 2), (8, 20), (4, 25)])
 def test_gimenez_lc_series_orders(torch_cuda, N, n_ss):
-    """Odd and even N, the largest N, supersample counts that leave masked
-    lanes in the two-lane blocks, and long supersample lists (n_ss >= 20)
-    that two threads share per pair."""
+    """Odd and even N, the largest N, supersample counts that leave the last
+    round of the evaluation partly filled, and supersample lists longer than
+    one batch of 16 (n_ss = 20, 25)."""
     import paper_1504_07433_gb300 as pt
     torch = torch_cuda
     wl = W.long_cadence(n_v=3, n_t=900, n_ss=n_ss, cadence=0.01)
@@ -96,6 +96,31 @@ def test_gimenez_lc_series_orders(torch_cuda, N, n_ss):
     ref = _oracle_lc(wl, 64)
     assert (ref < 1).sum() > 0
     assert np.max(np.abs(f - ref)) <= TOL
+
+@pytest.mark.parametrize("N,n_j,n_ss,n_t", [(16, 512, 40, 900), (1, 2, 3, 900)])
+def test_gimenez_extreme_plans(torch_cuda, N, n_j, n_ss, n_t):
+    """The largest plan (N = 16, n_j = 512: coefficient rows and round buffers
+    past the default 48 KB of shared memory) with three supersample batches,
+    and the smallest series (n_j = 2: no recurrence step at all)."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=2, n_t=n_t, n_ss=n_ss, cadence=0.01)
+    rng = np.random.default_rng(7 + N)
+    u = np.zeros((2, 1, N))
+    u[..., 0] = rng.uniform(0.3, 0.6, (2, 1))
+    if N > 1:
+        u[..., 1] = rng.uniform(0.0, 0.2, (2, 1))
+    if N > 2:
+        u[..., 2:] = rng.uniform(-0.01, 0.01, (2, 1, N - 2))
+    wl["ld"] = wl["ld_gim"] = u
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(N, n_j)
+    flux, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=n_ss, t_exp=wl["t_exp"])
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = _oracle_lc(wl, n_j)
+    assert (ref < 1).sum() > 0
+    assert np.max(np.abs(f - ref)) <= TOL
+
 
 def test_gimenez_ssr_and_multiband(torch_cuda):
     import paper_1504_07433_gb300 as pt
