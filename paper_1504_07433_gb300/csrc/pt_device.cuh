@@ -125,8 +125,11 @@ __device__ __forceinline__ void sincos_near0(float h, float *s, float *c)
 // so one Newton step usually converges.  The solution is written back.
 // FAST takes the Newton quotient with __fdividef (its denominator
 // 1 - e cos E lies in [1 - e, 1 + e]) and the final root as x * rsqrtf(x):
-// about one ulp more in z.
-template <bool FAST = false>
+// about one ulp more in z.  ROT takes sin and cos of dE/2 at the solution
+// from the last step's values (below) instead of a second series; the
+// per-supersample loops of the pair-list kernels gain from it, while in the
+// batched and tile kernels the extra live values cost more than the series.
+template <bool FAST = false, bool ROT = false>
 __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_iter, bool *bad, float *warm = nullptr)
 {
     if (r.ecc == 0.0f) {
@@ -164,18 +167,20 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
         warm[1] = dM;
         warm[2] = dEdM;
     }
-    // sin and cos of dE/2 at the solution: the last step's values rotated by
-    // -step/2 with cos(step/2) ~ 1 - step^2/8, sin(step/2) ~ step/2, instead
-    // of a new series.  The dropped terms are third order in step/2: the
-    // stopping rule accepts |step| <= sqrt(6e-8 |dE| / nq) (< 1e-3 unless e
-    // is tiny, where the Newton step itself is at most e |dM|), so they stay
-    // below 1e-10.
-    {
+    if (ROT) {
+        // sin and cos of dE/2 at the solution: the last step's values rotated
+        // by -step/2 with cos(step/2) ~ 1 - step^2/8, sin(step/2) ~ step/2.
+        // The dropped terms are third order in step/2: the stopping rule
+        // accepts |step| <= sqrt(6e-8 |dE| / nq) (< 1e-3 unless e is tiny,
+        // where the Newton step itself is at most e |dM|), so they stay
+        // below 1e-10.
         const float h = 0.5f * step;
         const float c = fmaf(-0.5f * h, h, 1.0f);
         const float sh1 = fmaf(-ch, h, sh * c);
         ch = fmaf(sh, h, ch * c);
         sh = sh1;
+    } else {
+        sincos_near0(0.5f * dE, &sh, &ch);
     }
     float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
     float dC = -r.cE * omc - r.sE * sn;

@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
 #pragma unroll 1
                 for (int s = sb0; s < s1; ++s) {
                     bool bad = false;
-                    const float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
+                    const float z = pt::orbit_z<true, true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
                     if (bad) ++nbad;
                     if (z < 1.0f + kk) {
                         const float cz = z / (1.0f + kk);
@@ -1280,7 +1280,7 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
 #pragma unroll 1
                 for (int s = sb0; s < s1; ++s) {
                     bool bad = false;
-                    const float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
+                    const float z = pt::orbit_z<true, true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
                     if (bad) ++nbad;
                     if (z < 1.0f + kk && kk > 0.0f) {
                         szp[c * MA_PPI + tid] = z;
