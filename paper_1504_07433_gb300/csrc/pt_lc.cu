@@ -1215,7 +1215,6 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
 {
     __shared__ GeomRec srec;
     __shared__ int sitem, sgeom, sbad;
-    __shared__ int sn[2];                    // entries inside, entries on the limb
     __shared__ int swarp[MA_PPI / 32];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
