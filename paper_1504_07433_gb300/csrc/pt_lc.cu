@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 //
 // Per geometry the table pass stores T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2
 // (Sec. 2.1.4: the z-independent factors).  Per (time, geometry) pair the
-// series kernel accumulates, for n = 0..N,
+// evaluation accumulates, for n = 0..N,
 //   alpha_n = b^2 (1 - c^2)^{nu+1} sum_j T_{n,j} G_j(nu+2, 1; c^2),
 // with only summations and multiplications in the z-dependent part
 // (Sec. 2.1.4).  Kernels:
@@ -337,12 +337,14 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
 //   gim_cheb_coef_kernel / gim_cheb_kernel  the series in a Chebyshev basis
 //                      shared by the orders (below): coefficients per
 //                      geometry, then persistent CTAs that take work items
-//                      from an atomic counter and give each pair one thread.
-// Every pair's flux is computed by the same threads in the same order
-// whatever CTA takes its item, so the result is deterministic.
+//                      from an atomic counter, evaluate the items' in-transit
+//                      supersamples as a dense list and sum each pair's
+//                      terms on the pair's own thread.
+// Every pair's sums are taken in the same order whatever thread evaluated
+// its terms and whatever CTA took its item, so the result is deterministic.
 // ---------------------------------------------------------------------------
 constexpr int GW_VT = 32;         // geometries per CTA of the window kernel (<= 32: one bit each)
-constexpr int GS_THREADS = 128;   // threads per CTA of the evaluation kernels (one pair each)
+constexpr int GS_THREADS = 128;   // threads per CTA of the evaluation kernels (one owned pair each)
 
 struct GimArgs {
     const float2 *tsplit;
@@ -359,7 +361,7 @@ struct GimArgs {
     float *flux;          // [rows][n_t]
     int *cnt;             // [n_geom] listed pairs per geometry
     int *pref;            // [n_geom + 1] work items before each geometry
-    int *ctr;             // next work item of the series kernel
+    int *ctr;             // next work item of the evaluation kernel
     int *list;            // [n_geom][n_t] time indices of listed pairs
     int ppi;              // pairs per work item (GS_THREADS or MA_PPI)
     int *n_bad;
@@ -575,7 +577,7 @@ __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A, TableJob J, i
 }
 
 // pref[g] = sum over g' < g of ceil(cnt[g'] / ppi); pref[n_geom] = total.
-// One CTA of 1024 threads; also rewinds the series kernel's item counter.
+// One CTA of 1024 threads; also rewinds the evaluation kernels' item counter.
 __global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_geom, int ppi, int *pref, int *ctr)
 {
     __shared__ int swarp[32];
@@ -1029,9 +1031,10 @@ size_t gim_cheb_smem(int n_j, int N, int n_ss)
 // Gimenez model interpolated in z (Sec. 3.3).  gim_zi_table_kernel evaluates
 // alpha_0..alpha_N of every geometry on its z nodes (n_in over [0, zb],
 // zb = max(1 - k, 0), then n_edge over (zb, 1 + k]) with the same Clenshaw
-// summation as the series kernel; gim_zi_kernel reads them by linear
-// interpolation for every listed (time, geometry) pair, with the same work
-// items, staging and passband combination as the series kernel.
+// summation as the coefficient kernel's node values; gim_zi_kernel reads
+// them by linear interpolation for every listed (time, geometry) pair (one
+// thread per pair), with the same work items and passband combination as
+// the series evaluation.
 // ---------------------------------------------------------------------------
 constexpr int ZI_MAX_VALUES = 16384;   // (n_in + n_edge)(N + 1) per geometry
 
