@@ -103,6 +103,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM traffic of one gim_cheb_kernel launch at 128 vectors of the long-cadence
+# workload, from its ncu capture (1.999 MB read + 6.9 KB written)
+TRAFFIC_128V = 1.999104e6 + 6.912e3
+
+
 def whole_job_rate(ms_local, pts_per_rank, ws, device="cpu"):
     """The job's time per step is the slowest rank's (a MAX all-reduce when
     ws > 1); the rate counts the points of every rank (weak scaling: each
@@ -668,7 +673,12 @@ def main():
     achieved = flops / (k_mean_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "gim_cheb_kernel (CUDA events recorded around its launch inside pt_gimenez)",
                 "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-                "traffic": None,
+                # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+                # capture of this kernel at 128 of the 256 vectors, doubled (every term of it - times,
+                # pair lists, records, coefficient rows - grows with the vectors); an ALU-bound
+                # kernel: lists and tables stay in L2
+                "traffic": (TRAFFIC_128V * n_v / 128.0) if (n_v, n_t, n_ss) == (256, 50000, 10) else None,
+                "traffic_source": "ncu capture of this kernel at 128 of the 256 vectors, scaled by 2",
                 "peak_source": "FP32 lanes 152 SM x 128 x 2 flop x %.0f MHz (%s sm_max_mhz)" % (sm_max, peak_src),
                 "algorithmic_flops_per_launch": flops, "in_transit_evaluations": n_intr,
                 "kernel_ms": k_mean_ms, "call_ms": g_mean_ms,
