@@ -736,7 +736,11 @@ __global__ void __launch_bounds__(128) gim_cheb_coef_kernel(const float4 *gtab, 
         const int m = threadIdx.x + r * blockDim.x;
         if (m >= n_j) break;
         float2 o2 = make_float2(no > 0 ? sum[r][0] + err[r][0] : 0.0f, no > 1 ? sum[r][1] + err[r][1] : 0.0f);
-        reinterpret_cast<float2 *>(dtab + ((size_t)g * n_j + m) * DS)[blockIdx.y] = o2;
+        float *row = dtab + ((size_t)g * n_j + m) * DS;
+        reinterpret_cast<float2 *>(row)[blockIdx.y] = o2;
+        // the last CTA of the geometry also clears the row's padding
+        if (blockIdx.y == gridDim.y - 1)
+            for (int q = 2 * (blockIdx.y + 1); q < DS; ++q) row[q] = 0.0f;
     }
 }
 
@@ -1697,7 +1701,9 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const floa
         if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_coef_kernel smem attribute");
         csm_configured = csm;
     }
-    gim_cheb_coef_kernel<<<dim3(A.n_geom, DS / 2), 128, csm, s>>>(T, A.N + 1, A.n_j, DS, cx, ccos, dtab);
+    // one CTA per pair of existing orders: (N + 2) / 2 per geometry (with
+    // 256 geometries and N = 8 the grid fits one wave of the GPU)
+    gim_cheb_coef_kernel<<<dim3(A.n_geom, (A.N + 2) / 2), 128, csm, s>>>(T, A.N + 1, A.n_j, DS, cx, ccos, dtab);
     int st = check_launch("gim_cheb_coef_kernel");
     if (st) return st;
     // evaluation: persistent
