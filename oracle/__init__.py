@@ -67,6 +67,8 @@ def _lib():
                 ("pto_gimenez_a", _D, [_I, _I]),
                 ("pto_gimenez_alpha", None, [_I, _I, _D, _D, _PD]),
                 ("pto_flux_gimenez", _D, [_I, _I, _D, _D, _PD]),
+                ("pto_ring_alpha", _D, [_I, _D, _D]),
+                ("pto_ring_flux", _D, [_I, _PD, _D, _D]),
                 ("pto_z_circ", _D, [_D, _D, _D, _D, _D]),
                 ("pto_kepler_newton", _I, [_D, _D, _I, _D, _PD]),
                 ("pto_z_ecc", _D, [_D, _D, _D, _D, _D, _D, _D, _I, _D, ctypes.POINTER(_I)]),
@@ -188,6 +190,19 @@ def gimenez_alpha(N, n_j, k, z):
 def flux_gimenez(k, z, u, n_j):
     u = _arr(u)
     return _lib().pto_flux_gimenez(u.size, n_j, k, z, _ptr(u))
+
+
+def ring_alpha(n, k, z):
+    """alpha_n from its definition: (1/pi) x the mu^n-weighted area of the
+    stellar disk covered by the planet, a ring integral (tanh-sinh)."""
+    return _lib().pto_ring_alpha(int(n), float(k), float(z))
+
+
+def ring_flux(u, k, z):
+    """Flux of the general law u_1..u_N (Eq. ld_general) from its definition:
+    1 - blocked / total light, both as ring integrals."""
+    u = _arr(u)
+    return _lib().pto_ring_flux(u.size, _ptr(u), float(k), float(z))
 
 
 def z_circ(t, t0, P, a, inc):

@@ -409,6 +409,142 @@ double pto_flux_gimenez(int N, int n_j, double k, double z, const double *u)
 }
 
 /* ------------------------------------------------------------------------
+ * The occulted flux from its definition (the quantity both models compute,
+ * Sec. 2.1.1 Eq. gimenez_flux and Sec. 2.2.1: the light of the limb-darkened
+ * stellar disk of unit radius blocked by an opaque disk of radius k whose
+ * centre is z away), written as a 1-D integral over rings of radius r:
+ *   blocked = int_0^1 w(r) r theta(r) dr,
+ * theta(r) = the angle of the ring that lies inside the planet's disk:
+ *   2 pi if r <= k - z;  0 if r >= z + k or r <= z - k;
+ *   2 acos((r^2 + z^2 - k^2) / (2 r z)) otherwise.
+ * With w = mu^n (mu = sqrt(1 - r^2)) this is pi alpha_n (the mu^n-weighted
+ * covered area of Eq. gimenez_alpha); with w = I(mu) of Eq. ld_general it
+ * gives f = 1 - blocked / F_tot, F_tot = int_0^1 I 2 pi r dr.  The series of
+ * Eq. gimenez converges to these values as N_J grows, so they measure its
+ * truncation error (the quantity of the paper's Fig. 1).
+ *
+ * Quadrature: tanh-sinh (Takahasi & Mori 1974) on each piece between the
+ * kinks |z - k|, z + k and 1, where the integrands have square-root end
+ * point behaviour; the step is halved until two levels agree to 1e-15.  The
+ * distance of a node to the nearer end is formed directly, so nodes that
+ * crowd an end point keep their accuracy.
+ * ---------------------------------------------------------------------- */
+typedef struct ring_weight {
+    int N;             /* mu^N (u == NULL) or the general law with N coefficients */
+    const double *u;   /* u_1..u_N of Eq. ld_general, or NULL */
+    double k, z;
+} ring_weight;
+
+/* 2 acos(c) for the ring at radius r, with 1 - c and 1 + c in factored form. */
+static double ring_theta(double r, double k, double z)
+{
+    if (r <= k - z) return 2.0 * PTO_PI;
+    if (r >= z + k || r <= z - k) return 0.0;
+    double omc = (k - r + z) * (k + r - z) / (2.0 * r * z);
+    double opc = (r + z - k) * (r + z + k) / (2.0 * r * z);
+    if (omc < 0.0) omc = 0.0;
+    if (opc < 0.0) opc = 0.0;
+    return 4.0 * atan2(sqrt(omc), sqrt(opc));
+}
+
+/* w(r) r theta(r); one_m_r = 1 - r, supplied separately for accuracy near r = 1. */
+static double ring_integrand(const ring_weight *W, double r, double one_m_r, int with_theta)
+{
+    double mu2 = one_m_r * (1.0 + r);
+    double mu = sqrt(mu2 > 0.0 ? mu2 : 0.0);
+    double w;
+    if (!W->u) {
+        w = pow(mu, (double)W->N);
+    } else {
+        w = 1.0;
+        double mun = 1.0;
+        for (int n = 1; n <= W->N; ++n) {
+            mun *= mu;
+            w -= W->u[n - 1] * (1.0 - mun);
+        }
+    }
+    double th = with_theta ? ring_theta(r, W->k, W->z) : 2.0 * PTO_PI;
+    return w * r * th;
+}
+
+static double tanh_sinh(const ring_weight *W, double a, double b, int with_theta)
+{
+    const double T = 4.0;
+    double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+    double h = 0.5, sum = 0.0, prev = 0.0;
+    for (int level = 0; level <= 12; ++level) {
+        /* level 0 takes every node k h; later levels only the new odd nodes */
+        double step = (level == 0) ? h : 2.0 * h;
+        double start = (level == 0) ? 0.0 : h;
+        double add = 0.0;
+        for (double t = start; t <= T; t += step) {
+            double u = 0.5 * PTO_PI * sinh(t);
+            double cu = cosh(u);
+            double wgt = 0.5 * PTO_PI * cosh(t) / (cu * cu);
+            double dist = (b - a) / (1.0 + exp(2.0 * u));   /* distance to the nearer end */
+            for (int side = (t == 0.0) ? 1 : 0; side < 2; ++side) {
+                double r, omr;
+                if (side == 0) {          /* node near a */
+                    r = a + dist;
+                    omr = 1.0 - r;
+                } else {                  /* node near b (t = 0: the midpoint) */
+                    r = (t == 0.0) ? mid : b - dist;
+                    omr = (b == 1.0 && t != 0.0) ? dist : 1.0 - r;
+                }
+                add += wgt * ring_integrand(W, r, omr, with_theta);
+            }
+        }
+        sum = (level == 0) ? add : sum + add;
+        double val = half * h * sum;
+        if (level >= 3 && fabs(val - prev) <= 1e-15 * (fabs(val) + 1e-300)) return val;
+        prev = val;
+        h *= 0.5;
+    }
+    return prev;
+}
+
+static double ring_blocked(const ring_weight *W)
+{
+    double k = W->k, z = fabs(W->z);
+    ring_weight V = *W;
+    V.z = z;
+    double pts[4];
+    int np = 0;
+    pts[np++] = 0.0;
+    double c1 = fabs(z - k), c2 = z + k;
+    if (c1 > 0.0 && c1 < 1.0) pts[np++] = c1;
+    if (c2 > 0.0 && c2 < 1.0 && c2 != c1) pts[np++] = c2;
+    pts[np++] = 1.0;
+    if (np == 4 && pts[1] > pts[2]) {
+        double s = pts[1];
+        pts[1] = pts[2];
+        pts[2] = s;
+    }
+    double tot = 0.0;
+    for (int i = 0; i + 1 < np; ++i)
+        if (pts[i + 1] > pts[i]) tot += tanh_sinh(&V, pts[i], pts[i + 1], 1);
+    return tot;
+}
+
+/* alpha_n(k, z) = (1/pi) x (mu^n-weighted area covered), from the definition. */
+double pto_ring_alpha(int n, double k, double z)
+{
+    if (k <= 0.0 || fabs(z) >= 1.0 + k) return 0.0;
+    ring_weight W = {n, NULL, k, z};
+    return ring_blocked(&W) / PTO_PI;
+}
+
+/* f(k, z) for the general law u_1..u_N (Eq. ld_general), from the definition:
+ * 1 - blocked light / total light, both integrated over rings. */
+double pto_ring_flux(int N, const double *u, double k, double z)
+{
+    if (k <= 0.0 || fabs(z) >= 1.0 + k) return 1.0;
+    ring_weight W = {N, u, k, z};
+    double tot = tanh_sinh(&W, 0.0, 1.0, 0);
+    return 1.0 - ring_blocked(&W) / tot;
+}
+
+/* ------------------------------------------------------------------------
  * Orbits (Sec. 1: circular orbits; eccentric orbits by Newton's method).
  * ---------------------------------------------------------------------- */
 
