@@ -18,10 +18,16 @@
  *   - `stream` is a cudaStream_t (0 = legacy default stream).  Calls are
  *     asynchronous with respect to the host: they enqueue kernels and return.
  *   - Return value: PT_OK, or a PT_ERR_* code for a host-detected error (bad
- *     size, null pointer, workspace too small) or a launch error.  A launch
- *     error's text is available from pt_last_error_string() (thread-local).
- *     Errors detected on the device (Newton not converged) are counted in an
- *     optional caller-provided device int, read after the stream syncs.
+ *     size, null pointer, workspace too small, a host-side value outside its
+ *     domain such as a negative exposure time) or a launch error.  The text of
+ *     the last error is available from pt_last_error_string() (thread-local).
+ *   - Conditions only the device can see come back through caller-provided
+ *     device ints: Newton solves that hit their step cap are counted in the
+ *     optional n_bad_dev of each call, and pt_domain_check() counts parameter
+ *     sets outside the model's domain.  The light-curve kernels themselves do
+ *     not check device-resident parameters (their results for out-of-domain
+ *     values are not specified); pt_status_read() synchronises a stream and
+ *     turns the two counters into PT_ERR_DOMAIN / PT_ERR_NOT_CONVERGED.
  *   - Layouts are row-major with time fastest: a flux cube is [n_v][n_b][n_t].
  *   - z of a point behind the star (the planet is not between the star and
  *     the observer) is PT_Z_BEHIND; its flux is 1.
@@ -50,8 +56,8 @@ typedef struct CUstream_st *pt_stream_t;
 enum {
     PT_OK = 0,
     PT_ERR_ARG = 1,           /* null pointer, negative size or inconsistent sizes */
-    PT_ERR_DOMAIN = 2,        /* parameter outside the supported domain */
-    PT_ERR_NOT_CONVERGED = 3, /* reserved: reported through n_bad counters */
+    PT_ERR_DOMAIN = 2,        /* parameter outside the supported domain (host check or pt_status_read) */
+    PT_ERR_NOT_CONVERGED = 3, /* Newton step cap hit (pt_status_read of an n_bad counter) */
     PT_ERR_CUDA = 4,          /* kernel launch or CUDA runtime error */
     PT_ERR_WORKSPACE = 5      /* work buffer null or smaller than required */
 };
@@ -90,6 +96,26 @@ typedef struct pt_orbit {
 } pt_orbit;
 
 /* ------------------------------------------------------------------------
+ * Parameter domain and device-side status.
+ *
+ * pt_domain_check counts, into *n_out_dev (device int; the caller zeroes it),
+ * the parameter sets outside the domain the model is defined and tested on:
+ *   t0 finite; 0 < P < 1e15; 1 < a < 1e7 (the orbit lies outside the star);
+ *   0 <= inc <= pi; e in [0, 0.95] and w finite when e is given;
+ *   0 < k <= 1e3 (NaN fails every test).
+ * k_dev holds n_k_per_v radius ratios per vector ([n_v] or [n_v][n_b]); a
+ * vector counts once per failing radius ratio, plus once if its orbit fails.
+ * Asynchronous on `stream`; reads its inputs only.
+ *
+ * pt_status_read synchronises `stream`, reads the two device counters (either
+ * may be NULL) and returns PT_ERR_DOMAIN if *n_domain_dev > 0, else
+ * PT_ERR_NOT_CONVERGED if *n_bad_dev > 0, else PT_OK; pt_last_error_string()
+ * then gives the count.  It does not reset the counters.
+ * ---------------------------------------------------------------------- */
+int pt_domain_check(const pt_orbit *orb, const float *k_dev, int n_k_per_v, int *n_out_dev, pt_stream_t stream);
+int pt_status_read(const int *n_bad_dev, const int *n_domain_dev, pt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Projected separation z(t) (Sec. 1: "circular and elliptic orbits (using
  * ... Newton's method ...)").  The paper gives no formula; the library uses
  * z = r sqrt(cos^2(w+f) + sin^2(w+f) cos^2 i), r = a(1 - e cos E), with the
@@ -119,6 +145,9 @@ int pt_z_ecc(const double *t_dev, int n_t, const pt_orbit *orb, int n_ss, double
  *   eta_d[i]  = eta_d,
  * so that f = 1 - [(1-c) lam_e + c lam_d + u2 eta_d] / (1 - u1/3 - u2/6)
  * with c = u1 + 2 u2.  All FP32 device arrays; k > 0.  Any output may be NULL.
+ * Accuracy: the flux formed from these terms is within 1e-6 of the FP64
+ * model for k <= 1 (every tested workload has k <= 0.3).  For k > 1 the
+ * brace cancels about tenfold in FP32 and the bound is 3e-6.
  * ---------------------------------------------------------------------- */
 int pt_ma_terms(const float *k_dev, const float *z_dev, size_t n, float *lam_e_dev, float *lam_d_dev,
                 float *eta_d_dev, pt_stream_t stream);
@@ -145,6 +174,8 @@ int pt_ma_terms(const float *k_dev, const float *z_dev, size_t n, float *lam_e_d
  * (the factoring of Sec. 2.2.2); with k_per_band == 1 every passband has its
  * own radius ratio and is evaluated as its own geometry.
  * At least one of flux_dev and ssr_dev must be non-NULL.
+ * Accuracy: fluxes within 1e-6 of the FP64 model for k <= 1 (3e-6 above,
+ * as for pt_ma_terms).  PT_ERR_DOMAIN for t_exp < 0 or not finite.
  * ---------------------------------------------------------------------- */
 size_t pt_ma_quad_work_bytes(int n_t, int n_v, int n_b, int k_per_band);
 
@@ -358,9 +389,14 @@ int pt_sur_model_error(pt_sur_model model, int *err_host);
  *
  * Scratch comes from a static device array of PT_MA_NOALLOC_SCRATCH_BYTES
  * (4 MiB) that every GPU loading the library keeps until the process exits.
- * A problem whose pt_ma_quad_work_bytes() exceeds it is rejected with
- * PT_ERR_WORKSPACE (see pt_last_error_string()) -- roughly n_t <= 400,000 for
- * a few hundred vectors, less with SSR output over many rows.
+ * The call runs the tile kernel, whose scratch is, with each term rounded up
+ * to a multiple of 256 bytes,
+ *   96 n_geom + 8 n_t + 4 n_v n_b ceil(n_t / 256)
+ * (n_geom = n_v, or n_v n_b with k_per_band); this is less than
+ * pt_ma_quad_work_bytes(), which sizes pt_ma_quad's pair lists.  A problem
+ * above the limit is rejected with PT_ERR_WORKSPACE (see
+ * pt_last_error_string()): for one passband that is about n_t > 375,000 at
+ * 200 vectors, or n_t > 173,000 at 1,000.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  The call allocates and frees nothing.

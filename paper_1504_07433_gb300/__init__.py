@@ -19,6 +19,7 @@ import os
 from . import build as _build_mod
 
 __all__ = ["load_library", "Orbit", "Theta", "orbit_to_device", "z_circ", "z_ecc", "ma_terms", "ma_quad",
+           "domain_check", "status_read",
            "MATable", "ma_terms_interp", "ma_quad_interp", "gimenez_zi",
            "ma_quad_work_bytes", "GimenezPlan", "gimenez", "gimenez_alpha", "ma_quad_bwd", "transit_ssr",
            "PTError", "Z_BEHIND"]
@@ -73,6 +74,8 @@ def load_library(build_if_missing: bool = False):
         "pt_z_circ": (_c_int, [P, _c_int, ctypes.POINTER(Orbit), _c_int, _c_double, P, P]),
         "pt_z_ecc": (_c_int, [P, _c_int, ctypes.POINTER(Orbit), _c_int, _c_double, _c_int, _c_double, P, P, P]),
         "pt_ma_terms": (_c_int, [P, P, _c_size, P, P, P, P]),
+        "pt_domain_check": (_c_int, [ctypes.POINTER(Orbit), P, _c_int, P, P]),
+        "pt_status_read": (_c_int, [P, P, P]),
         "pt_ma_quad_work_bytes": (_c_size, [_c_int, _c_int, _c_int, _c_int]),
         "pt_ma_quad": (_c_int, [P, _c_int, ctypes.POINTER(Orbit), P, _c_int, P, _c_int, _c_int, _c_double, _c_int,
                                 P, P, P, P, P, _c_size, P, P]),
@@ -194,6 +197,29 @@ def ma_terms(k, z):
     ed = torch.empty_like(z)
     _check(lib.pt_ma_terms(_ptr(k), _ptr(z), z.numel(), _ptr(le), _ptr(ld), _ptr(ed), _stream()), "pt_ma_terms")
     return le, ld, ed
+
+
+def domain_check(orb, k, n_out=None):
+    """pt_domain_check: count the parameter sets outside the model's domain
+    into a device int (returned; pass n_out to accumulate into your own).
+    k is [n_v] or [n_v, n_b]."""
+    torch = _torch()
+    lib = load_library()
+    o, n_v = _orbit_struct(orb)
+    if n_out is None:
+        n_out = torch.zeros(1, dtype=torch.int32, device=orb["t0"].device)
+    per_v = 1 if k.dim() == 1 else int(k.shape[1])
+    _check(lib.pt_domain_check(ctypes.byref(o), _ptr(k.contiguous()), per_v, _ptr(n_out), _stream()),
+           "pt_domain_check")
+    return n_out
+
+
+def status_read(n_bad=None, n_domain=None):
+    """pt_status_read: synchronise the current stream and turn the device
+    counters into a status; returns (status, message)."""
+    lib = load_library()
+    st = int(lib.pt_status_read(_ptr(n_bad), _ptr(n_domain), _stream()))
+    return st, (lib.pt_last_error_string().decode() if st else "")
 
 
 def ma_quad_work_bytes(n_t, n_v, n_b, k_per_band=False):

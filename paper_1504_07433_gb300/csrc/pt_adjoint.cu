@@ -436,6 +436,8 @@ int pt_ma_quad_bwd(const double *t, int n_t, const pt_theta *th, int n_ss, doubl
 {
     if (!th || th->n_v < 0 || n_t < 0 || n_ss < 1 || n_ss > 256 || max_iter < 1 || max_iter > 64)
         return PT_ERR_ARG;
+    if (!(t_exp >= 0.0 && t_exp < 1.0e30))
+        return pt_internal::set_error(PT_ERR_DOMAIN, "pt_ma_quad_bwd", "exposure time must be finite and >= 0");
     if (n_t == 0 || th->n_v == 0) return PT_OK;
     if (!th->t0 || !th->P || !th->a || !th->b || !th->k || !th->u1 || !th->u2) return PT_ERR_ARG;
     if ((th->e == nullptr) != (th->w == nullptr)) return PT_ERR_ARG;

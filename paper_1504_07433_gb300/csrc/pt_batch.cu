@@ -436,6 +436,8 @@ int pt_batch_plan_create(const pt_batch_desc *d, int autotune, pt_batch_plan *ou
     if (!d->flux && !d->ssr) return PT_ERR_ARG;
     if (d->k_mode != 0 && d->k_mode != 1) return PT_ERR_ARG;
     if (d->ssr && !d->y) return PT_ERR_ARG;
+    if (!(d->t_exp >= 0.0 && d->t_exp < 1.0e30))
+        return pt_internal::set_error(PT_ERR_DOMAIN, "pt_batch_plan_create", "exposure time must be finite and >= 0");
     if (d->lc_offsets[0] != 0 || d->lc_offsets[d->n_lc] != d->n_t) return PT_ERR_ARG;
     for (int j = 0; j < d->n_lc; ++j)
         if (d->lc_offsets[j + 1] < d->lc_offsets[j]) return PT_ERR_ARG;

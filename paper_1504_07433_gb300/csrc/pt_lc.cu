@@ -1,20 +1,25 @@
 // pt_lc.cu -- light-curve kernels and their C ABI (include/pt.h).
 //
-// Kernel structure of the fused light-curve path (Secs. 2.1, 2.2, 3.2, 3.4):
-//   setup_kernel   per geometry: FP64 conjunction anchor, double-float t0/P,
-//                  a conservative transit window; per time: double-float split.
-//   ma_lc_kernel / gim_lc_kernel, one CTA per (256-time tile, VT geometries):
-//     A. every (time, geometry) pair: phase reduction + window test; pairs in
-//        the window are appended to a shared-memory queue (compaction, so
-//        the expensive branches run on full warps);
-//     B. queued pairs are expanded to (pair, supersample) units; each unit
-//        computes z and the limb-darkening-free terms (lambda_e, lambda_d,
-//        eta_d for MA; alpha_0..alpha_N for Gimenez); sums over the
-//        supersamples are formed in a fixed order (deterministic);
-//     C. every output: the per-passband limb-darkening combination and a
-//        coalesced store of the flux cube and/or a deterministic block
-//        reduction of the weighted squared residuals.
-//   ssr_reduce_kernel: sums the per-tile residual partials in a fixed order.
+// Kernels of the fused light-curve path (Secs. 2.1, 2.2, 3.2, 3.4):
+//   setup_kernel        per geometry: conjunction anchor, double-float t0/P and
+//                       a conservative transit window; per time: double-float split.
+//   gim_window_kernel   window test of every (time, geometry) pair; the pairs in
+//                       the window go to per-geometry lists, all others get flux 1
+//                       (its leading CTAs also build the Gimenez tables).
+//   gim_scan_kernel     work items of 128 listed pairs per geometry.
+//   ma_pairs_kernel     Mandel-Agol: per item, the in-transit supersamples packed
+//                       into one dense list, evaluated, summed per pair in
+//                       supersample order, limb darkening per passband, stores.
+//   gim_cheb_coef_kernel, gim_cheb_kernel
+//                       Gimenez: the series in a Chebyshev basis (coefficients
+//                       per geometry, then the evaluation over the dense lists).
+//   gim_zi_table_kernel, gim_zi_kernel
+//                       Gimenez interpolated in z (Sec. 3.3).
+//   ma_lc_kernel        the tile kernel (256 times x 8 geometries per CTA) of the
+//                       interpolated and allocation-free Mandel-Agol calls.
+//   ssr_rows_kernel / ssr_reduce_kernel
+//                       residual sums in a fixed order.
+// Every sum is formed in a fixed order, so results are bitwise reproducible.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -1552,6 +1557,9 @@ __global__ void z_ecc_kernel(const double *t, int n_t, const double *t0, const d
     z[(size_t)v * n_t * n_ss + idx] = out;
 }
 
+// Exposure time: finite and non-negative (the supersamples of Sec. 3.2 span it).
+bool exposure_ok(double t_exp) { return t_exp >= 0.0 && t_exp < 1.0e30; }
+
 int check_orbit(const pt_orbit *orb, bool need_ecc)
 {
     if (!orb || orb->n_v < 0) return PT_ERR_ARG;
@@ -1762,6 +1770,33 @@ int launch_cheb(const GimArgs &A, const float4 *T, const float *cx, const float 
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// Parameter domain (include/pt.h, pt_domain_check): counts the geometries
+// (vector, or vector and passband when k is per passband) whose parameters
+// lie outside it.  Reads its inputs only.
+__global__ void domain_kernel(const double *t0, const double *P, const float *a, const float *inc, const float *e,
+                              const float *w, const float *k, int n_v, int n_kv, int *n_out)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (g < n_v * n_kv) {
+        int v = g / n_kv;
+        const float kk = k[g];
+        bad = !(kk > 0.0f && kk <= 1.0e3f);
+        if (g % n_kv == 0) {
+            const double tv = t0[v], pv = P[v];
+            const float av = a[v], iv = inc[v];
+            bad |= !(fabs(tv) < 1.0e15) || !(pv > 0.0 && pv < 1.0e15) || !(av > 1.0f && av < 1.0e7f) ||
+                   !(iv >= 0.0f && iv <= 3.14159274f);
+            if (e) {
+                const float ev = e[v], wv = w[v];
+                bad |= !(ev >= 0.0f && ev <= 0.95f) || !(fabsf(wv) < 1.0e6f);
+            }
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(n_out, __popc(m));
+}
+
 extern "C" {
 
 int pt_version(void) { return 100; }
@@ -1787,6 +1822,7 @@ int pt_z_circ(const double *t, int n_t, const pt_orbit *orb, int n_ss, double t_
     int st = check_orbit(orb, false);
     if (st) return st;
     if (n_t < 0 || n_ss < 1 || (n_t > 0 && (!t || !z))) return PT_ERR_ARG;
+    if (!exposure_ok(t_exp)) return pt_internal::set_error(PT_ERR_DOMAIN, "pt_z_circ", "exposure time must be finite and >= 0");
     if (n_t == 0 || orb->n_v == 0) return PT_OK;
     if ((long long)n_t * n_ss > 0x7fffffffLL || orb->n_v > 65535) return PT_ERR_ARG;
     dim3 grid((n_t * n_ss + 255) / 256, orb->n_v);
@@ -1802,6 +1838,7 @@ int pt_z_ecc(const double *t, int n_t, const pt_orbit *orb, int n_ss, double t_e
     if (st) return st;
     if (n_t < 0 || n_ss < 1 || max_iter < 1 || max_iter > 1000 || !(tol > 0.0) || (n_t > 0 && (!t || !z)))
         return PT_ERR_ARG;
+    if (!exposure_ok(t_exp)) return pt_internal::set_error(PT_ERR_DOMAIN, "pt_z_ecc", "exposure time must be finite and >= 0");
     if (n_t == 0 || orb->n_v == 0) return PT_OK;
     if ((long long)n_t * n_ss > 0x7fffffffLL || orb->n_v > 65535) return PT_ERR_ARG;
     dim3 grid((n_t * n_ss + 255) / 256, orb->n_v);
@@ -1820,15 +1857,55 @@ int pt_ma_terms(const float *k, const float *z, size_t n, float *le, float *ld, 
     return check_launch("pt_ma_terms");
 }
 
+int pt_domain_check(const pt_orbit *orb, const float *k, int n_k_per_v, int *n_out, pt_stream_t stream)
+{
+    int st = check_orbit(orb, false);
+    if (st) return st;
+    if (n_k_per_v < 1 || !n_out) return PT_ERR_ARG;
+    if (orb->n_v == 0) return PT_OK;
+    if (!k || (long long)orb->n_v * n_k_per_v > 0x7fffffffLL) return PT_ERR_ARG;
+    const int n = orb->n_v * n_k_per_v;
+    domain_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(orb->t0, orb->P, orb->a, orb->inc, orb->e,
+                                                                    orb->w, k, orb->n_v, n_k_per_v, n_out);
+    return check_launch("pt_domain_check");
+}
+
+int pt_status_read(const int *n_bad, const int *n_domain, pt_stream_t stream)
+{
+    int h[2] = {0, 0};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int *src[2] = {n_domain, n_bad};
+    for (int i = 0; i < 2; ++i) {
+        if (!src[i]) continue;
+        cudaError_t e = cudaMemcpyAsync(&h[i], src[i], sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return set_cuda_error(e, "pt_status_read");
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_cuda_error(e, "pt_status_read");
+    if (h[0] > 0) {
+        snprintf(g_last_error, sizeof(g_last_error), "pt_status_read: %d geometries outside the parameter domain",
+                 h[0]);
+        return PT_ERR_DOMAIN;
+    }
+    if (h[1] > 0) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "pt_status_read: %d Newton solves stopped at the step cap before converging", h[1]);
+        return PT_ERR_NOT_CONVERGED;
+    }
+    return PT_OK;
+}
+
 static int lc_common_check(const double *t, int n_t, const pt_orbit *orb, const float *k, int k_per_band,
-                           const float *ld, int n_b, int n_ss, int max_iter, const float *y, float *flux,
-                           float *ssr, void *work)
+                           const float *ld, int n_b, int n_ss, double t_exp, int max_iter, const float *y,
+                           float *flux, float *ssr, void *work)
 {
     int st = check_orbit(orb, false);
     if (st) return st;
     if (n_t < 0 || n_b < 1 || n_ss < 1 || n_ss > MAX_SS || max_iter < 1 || max_iter > MAX_NEWTON)
         return PT_ERR_ARG;
     if (k_per_band != 0 && k_per_band != 1) return PT_ERR_ARG;
+    if (!exposure_ok(t_exp))
+        return pt_internal::set_error(PT_ERR_DOMAIN, "light curve", "exposure time must be finite and >= 0");
     if (n_t == 0 || orb->n_v == 0) return PT_OK;   // nothing to evaluate
     if (!flux && !ssr) return PT_ERR_ARG;
     if (!t || !k || !ld) return PT_ERR_ARG;
@@ -1880,7 +1957,7 @@ static int ma_quad_list(const double *t, int n_t, const pt_orbit *orb, const flo
                         const float *wt, float *flux, float *ssr, void *work, size_t work_bytes, int *n_bad,
                         pt_stream_t stream)
 {
-    int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, max_iter, y, flux, ssr, work);
+    int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, flux, ssr, work);
     if (st) return st;
     if (n_t == 0 || orb->n_v == 0) return PT_OK;
     WorkLayout L = work_layout(n_t, orb->n_v, n_b, k_per_band, 1, 0);
@@ -1952,7 +2029,7 @@ static int ma_quad_impl(const pt_ma_table_s *tab, const double *t, int n_t, cons
                         const float *y, const float *wt, float *flux, float *ssr, void *work, size_t work_bytes,
                         int *n_bad, pt_stream_t stream)
 {
-    int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, max_iter, y, flux, ssr, work);
+    int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, flux, ssr, work);
     if (st) return st;
     if (n_t == 0 || orb->n_v == 0) return PT_OK;
     WorkLayout L = work_layout(n_t, orb->n_v, n_b, k_per_band, 0, 0);
@@ -2204,7 +2281,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     const bool zi = n_in > 0;
     if (zi && (n_in < 2 || n_edge < 1 || (size_t)(n_in + n_edge) * (plan->N + 1) > (size_t)ZI_MAX_VALUES))
         return PT_ERR_ARG;
-    int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, max_iter, y, flux, ssr, work);
+    int st = lc_common_check(t, n_t, orb, k, k_per_band, ld, n_b, n_ss, t_exp, max_iter, y, flux, ssr, work);
     if (st) return st;
     if (n_t == 0 || orb->n_v == 0) return PT_OK;
     const int NP1 = plan->N + 1;

@@ -67,6 +67,17 @@ def test_host_side_argument_checks(lib):
     assert L.pt_ma_quad(ctypes.c_void_p(8), 10, ctypes.byref(o3), ctypes.c_void_p(8), 0, ctypes.c_void_p(8), 1,
                         0, 0.0, 16, None, None, ctypes.c_void_p(8), None, ctypes.c_void_p(8), 1 << 20, None,
                         None) == 1
+    # a negative or non-finite exposure time -> PT_ERR_DOMAIN, before any CUDA call
+    for bad_exp in (-0.01, float("nan"), float("inf")):
+        assert L.pt_ma_quad(ctypes.c_void_p(8), 10, ctypes.byref(o3), ctypes.c_void_p(8), 0, ctypes.c_void_p(8), 1,
+                            3, bad_exp, 16, None, None, ctypes.c_void_p(8), None, ctypes.c_void_p(8), 1 << 20, None,
+                            None) == 2
+        assert L.pt_z_circ(ctypes.c_void_p(8), 10, ctypes.byref(o3), 3, bad_exp, ctypes.c_void_p(8), None) == 2
+    assert b"exposure" in L.pt_last_error_string()
+    # domain check: a missing counter or radius-ratio array is an argument error
+    assert L.pt_domain_check(ctypes.byref(o3), ctypes.c_void_p(8), 1, None, None) == 1
+    assert L.pt_domain_check(ctypes.byref(o3), None, 1, ctypes.c_void_p(8), None) == 1
+    assert L.pt_domain_check(ctypes.byref(o3), ctypes.c_void_p(8), 0, ctypes.c_void_p(8), None) == 1
     # Gimenez plan arguments are checked before allocation
     h = ctypes.c_void_p()
     assert L.pt_gim_plan_create(0, 100, ctypes.byref(h)) == 1
