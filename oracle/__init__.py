@@ -80,6 +80,7 @@ def _lib():
                                         _I, _I, _D, _PD, _I]),
                 ("pto_ssr", None, [_PD, _PD, _PD, _I, _I, _I, _PD]),
                 ("pto_max_threads", _I, []),
+                ("pto_ma_terms_batch", None, [ctypes.c_long, _PD, _PD, _PD, _I]),
                 ("pto_overlap_derivs", None, [_D, _D, _PD]),
                 ("pto_flux_theta", _D, [_D, _PD, _I, _D]),
                 ("pto_flux_grad", _D, [_D, _PD, _I, _D, _PD]),
@@ -157,6 +158,14 @@ def ma_terms(p, z):
     """(lambda_e, lambda_d, eta_d) of Mandel & Agol (lambda_d without 2/3 Theta(p-z))."""
     out = np.zeros(3)
     _lib().pto_ma_terms(p, z, _ptr(out))
+    return out
+
+
+def ma_terms_batch(p, z, n_threads=0):
+    """ma_terms at many points: [n, 3] of (lambda_e, lambda_d, eta_d)."""
+    p, z = (np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel()) for x in np.broadcast_arrays(p, z))
+    out = np.zeros((z.size, 3))
+    _lib().pto_ma_terms_batch(z.size, _ptr(p), _ptr(z), _ptr(out), int(n_threads))
     return out
 
 

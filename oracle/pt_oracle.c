@@ -47,6 +47,11 @@
 #endif
 
 #define PTO_PI 3.14159265358979323846
+
+/* Threads of an OpenMP loop: n_threads if positive, else the default. */
+#ifdef _OPENMP
+static int pto_nthreads(int n_threads) { return n_threads > 0 ? n_threads : omp_get_max_threads(); }
+#endif
 #define PTO_Z_BEHIND 1.0e30
 #define PTO_CARLSON_TOL 1e-10
 
@@ -652,8 +657,7 @@ int pto_lc_ma(const double *t, int n_t, const double *t0, const double *P, const
 {
     int nbad = 0;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad) num_threads(pto_nthreads(n_threads))
 #endif
     for (int v = 0; v < n_v; ++v) {
         for (int i = 0; i < n_t; ++i) {
@@ -687,8 +691,7 @@ int pto_lc_ma_khat(const double *t, int n_t, const double *t0, const double *P, 
 {
     int nbad = 0;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad) num_threads(pto_nthreads(n_threads))
 #endif
     for (int v = 0; v < n_v; ++v) {
         double kh = 0.0;
@@ -724,8 +727,7 @@ int pto_lc_ma_interp(const double *tab, double k_lo, double k_hi, int n_k, int n
 {
     int nbad = 0;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad) num_threads(pto_nthreads(n_threads))
 #endif
     for (int v = 0; v < n_v; ++v) {
         for (int i = 0; i < n_t; ++i) {
@@ -755,8 +757,7 @@ int pto_lc_gimenez(const double *t, int n_t, const double *t0, const double *P, 
 {
     int nbad = 0;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad) num_threads(pto_nthreads(n_threads))
 #endif
     for (int v = 0; v < n_v; ++v) {
         for (int i = 0; i < n_t; ++i) {
@@ -838,8 +839,7 @@ int pto_lc_gimenez_zi(const double *t, int n_t, const double *t0, const double *
     int nbad = 0;
     int nz = n_in + n_edge;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad) num_threads(pto_nthreads(n_threads))
 #endif
     for (int v = 0; v < n_v; ++v) {
         double *tab = (double *)malloc(sizeof(double) * (size_t)nz * (N + 1) * n_b);
@@ -895,6 +895,15 @@ void pto_ssr(const double *flux, const double *y, const double *wt, int n_v, int
             }
             ssr[(size_t)v * n_b + b] = s;
         }
+}
+
+/* pto_ma_terms at n points (k[i], z[i]); out is [n][3].  OpenMP over points. */
+void pto_ma_terms_batch(long n, const double *k, const double *z, double *out, int n_threads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(pto_nthreads(n_threads))
+#endif
+    for (long i = 0; i < n; ++i) pto_ma_terms(k[i], z[i], out + 3 * i);
 }
 
 int pto_max_threads(void)
@@ -1075,8 +1084,7 @@ void pto_ssr_grad(const double *t, int n_t, const double *th, int n_v, int n_ss,
                   const double *y, const double *wt, double *ssr, double *grad, int n_threads)
 {
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) num_threads(pto_nthreads(n_threads))
 #endif
     for (int v = 0; v < n_v; ++v) {
         double s = 0.0, G[9] = {0}, g[9];

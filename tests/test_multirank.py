@@ -62,3 +62,13 @@ def test_single_rank_rate():
     import bench
     ms, rate = bench.whole_job_rate(0.5, 2000, 1)
     assert ms == 0.5 and rate == pytest.approx(2000 / 0.5e-3)
+
+
+def test_bench_series_depth_is_the_truncation_study_default():
+    """The benchmark's Gimenez depth is the one the truncation study picks
+    (tests/golden/gimenez_truncation.json): the smallest within 1e-5 over the
+    long-cadence priors."""
+    import json
+    import bench
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "gimenez_truncation.json")))
+    assert bench.N_J == g["default_n_j"]

@@ -4,9 +4,10 @@ Callers that cannot allocate device memory (their device memory belongs to
 a fixed pool of their own, or their sampling loop must not stall on an
 allocation) use this entry point; it takes its scratch from a static device
 array inside the library.  These tests call it through the C ABI and check
-it against pt_ma_quad (same kernels, caller-provided work buffer) on two
-different calls in a row, so that anything a call failed to overwrite in
-the shared scratch would show up in the second one.
+it against pt_ma_quad (caller-provided work buffer) on two different calls
+in a row, so that anything a call failed to overwrite in the shared scratch
+would show up in the second one, and both calls against the FP64 oracle
+directly (its tile kernel is reached by no other exact-model entry point).
 
 This file is collected last on purpose; it also runs alone in a fresh
 process (the first call on the device performs the scratch look-up).
@@ -16,8 +17,9 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1504_07433_gb300 import workloads as W
-from tests.helpers import gpu_inputs
+from tests.helpers import f32, gpu_inputs, oracle_orbit
 
 pytestmark = pytest.mark.gpu
 
@@ -70,6 +72,9 @@ def test_noalloc_matches_work_buffer_entry_point_twice(env):
     # |sum (y - f1)^2 - sum (y - f2)^2| <= sum (2 |y - f| TOL + TOL^2)
     bound = (2.0 * TOL * torch.abs(y[None] - f_ref).double().sum(dim=2) + t.numel() * TOL ** 2)
     assert torch.all(torch.abs(s_na.double() - s_ref.double()) <= bound)
+    ref = oracle.lc_ma(wl["t"], oracle_orbit(wl["orbit"]), f32(wl["k"]), f32(wl["ld"]), n_ss=10,
+                       t_exp=wl["t_exp"])[0]
+    assert np.max(np.abs(f_na.cpu().numpy().astype(np.float64) - ref)) <= TOL
     # call 2, straight after: a different, smaller circular problem with per-band k
     wl2 = W.batched(n_walkers=7, n_pb=3, n_lc=2, len_lo=300, len_hi=600)
     t2, orb2, k2, ld2 = gpu_inputs(wl2)
@@ -77,6 +82,8 @@ def test_noalloc_matches_work_buffer_entry_point_twice(env):
     f_ref2, _ = pt.ma_quad(t2, orb2, k2, ld2)
     assert (f_ref2 < 1).sum().item() > 0
     assert torch.max(torch.abs(f_na2 - f_ref2)).item() <= TOL
+    ref2 = oracle.lc_ma(wl2["t"], oracle_orbit(wl2["orbit"]), f32(wl2["k"]), f32(wl2["ld"]))[0]
+    assert np.max(np.abs(f_na2.cpu().numpy().astype(np.float64) - ref2)) <= TOL
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(env):
