@@ -62,22 +62,35 @@ __device__ __forceinline__ void ellke(float kc, float *K, float *E)
 
 // S(m) = int_0^{pi/2} sin^2 cos^2 / sqrt(1 - m sin^2): binomial series below
 // m = 1/2 (terms fall as m^n n^-2; 24 terms reach 1e-9), closed form in K, E
-// at and above it.
+// at and above it.  Term n is c_n (w_n - w_{n+1}) m^n with c_n the binomial
+// coefficients of (1 - x)^(-1/2) and w_n = int_0^{pi/2} sin^(2n) = (pi/2)
+// (2n-1)!!/(2n)!!; the coefficients are constants, formed at compile time,
+// and the sum runs by Horner's rule.
+struct S2C2Coef {
+    float a[24];
+};
+
+constexpr S2C2Coef make_s2c2()
+{
+    S2C2Coef r{};
+    double c = 1.0, w1 = 0.25 * 3.14159265358979323846, w2 = w1 * 0.75;
+    for (int n = 0; n < 24; ++n) {
+        r.a[n] = (float)(c * (w1 - w2));
+        c *= (2.0 * n + 1.0) / (2.0 * n + 2.0);
+        double w3 = w2 * (2.0 * n + 5.0) / (2.0 * n + 6.0);
+        w1 = w2;
+        w2 = w3;
+    }
+    return r;
+}
+
 __device__ __forceinline__ float s2c2_int(float m, float K, float E)
 {
     if (m < 0.5f) {
-        float w1 = 0.25f * PI_F;          // w_1 = (pi/2)(1/2)
-        float w2 = w1 * 0.75f;            // w_2 = w_1 * 3/4
-        float c = 1.0f, mn = 1.0f, s = 0.0f;
-#pragma unroll 4
-        for (int n = 0; n < 24; ++n) {
-            s = fmaf(c * mn, w1 - w2, s);
-            c *= (2.0f * n + 1.0f) / (2.0f * n + 2.0f);
-            mn *= m;
-            float w3 = w2 * (2.0f * n + 5.0f) / (2.0f * n + 6.0f);
-            w1 = w2;
-            w2 = w3;
-        }
+        constexpr S2C2Coef C = make_s2c2();
+        float s = C.a[23];
+#pragma unroll
+        for (int n = 22; n >= 0; --n) s = fmaf(s, m, C.a[n]);
         return s;
     }
     return ((2.0f - m) * E - 2.0f * (1.0f - m) * K) / (3.0f * m * m);
@@ -249,7 +262,7 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
         float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
         float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
         float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
-        float step = F / Fp;
+        float step = __fdividef(F, Fp);   // Fp lies in [1 - e, 1 + e]
         dE -= step;
         if (fabsf(step) <= 4e-7f * fabsf(dE) + 1e-12f) {
             conv = true;
@@ -349,7 +362,7 @@ __global__ void tsplit_kernel(const double *t, int n, float2 *out)
     }
 }
 
-__global__ void __launch_bounds__(TB) ma_bwd_kernel(BwdArgs A)
+__global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
 {
     __shared__ VecConst sc;
     __shared__ float sred[TB / 32][10];

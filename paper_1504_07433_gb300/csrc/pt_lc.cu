@@ -17,7 +17,7 @@
 //                       Gimenez interpolated in z (Sec. 3.3).
 //   ma_lc_kernel        the tile kernel (256 times x 8 geometries per CTA) of the
 //                       interpolated and allocation-free Mandel-Agol calls.
-//   ssr_rows_kernel / ssr_reduce_kernel
+//   ssr_part_kernel / ssr_reduce_kernel
 //                       residual sums in a fixed order.
 // Every sum is formed in a fixed order, so results are bitwise reproducible.
 #include <cuda_runtime.h>
@@ -770,9 +770,10 @@ size_t gim_cheb_coef_smem(int n_j)
 //     entry, T_{m+1} = 2y T_m - T_{m-1}, and one FMA per order n and m for
 //     d_{n,m} T_m (scalar FMAs: on this part they sustain more FMAs per
 //     cycle than the two-lane form).  Rounds of GS_GMAX = 4 entries per
-//     thread while at least 4 GS_THREADS entries are left, then rounds of 2
-//     (each coefficient load serves the thread's entries; smaller rounds
-//     leave less of the last one empty).  The S_n go to shared memory;
+//     thread while at least 4 GS_THREADS entries are left, then one round of
+//     the fewest entries per thread (1 to 3) that holds the rest (each
+//     coefficient load serves the thread's entries).  The S_n go to shared
+//     memory;
 //  3. each thread adds its own pair's b^2 q^(n+4) S_n to alpha_n in
 //     supersample order, so the sums do not depend on the rounds.
 // After the last batch, the passband combination of Sec. 2.1.3.
@@ -860,9 +861,12 @@ __device__ __forceinline__ void cheb_round(const float *sd, int nj, const float2
 #pragma unroll
             for (int u = 0; u < G; u += 4)
                 *reinterpret_cast<float4 *>(dst + u) = make_float4(acc[u][n], acc[u + 1][n], acc[u + 2][n], acc[u + 3][n]);
-        } else {
+        } else if (G % 2 == 0) {
 #pragma unroll
             for (int u = 0; u < G; u += 2) *reinterpret_cast<float2 *>(dst + u) = make_float2(acc[u][n], acc[u + 1][n]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < G; ++u) dst[u] = acc[u][n];
         }
     }
 }
@@ -976,12 +980,19 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
                 // 2. a round of series values; its size from what is left
                 const int rem = n_e - r0;
                 int size;
-                if (rem >= GS_GMAX * GS_THREADS) {
+                const int gfit = (rem + GS_THREADS - 1) / GS_THREADS;   // the last round fits what is left
+                if (gfit >= GS_GMAX) {
                     cheb_round<NP1, GS_GMAX>(sd, nj, syq, sst, sS, r0, n_e);
                     size = GS_GMAX * GS_THREADS;
-                } else {
+                } else if (gfit == 3) {
+                    cheb_round<NP1, 3>(sd, nj, syq, sst, sS, r0, n_e);
+                    size = 3 * GS_THREADS;
+                } else if (gfit == 2) {
                     cheb_round<NP1, 2>(sd, nj, syq, sst, sS, r0, n_e);
                     size = 2 * GS_THREADS;
+                } else {
+                    cheb_round<NP1, 1>(sd, nj, syq, sst, sS, r0, n_e);
+                    size = GS_THREADS;
                 }
                 __syncthreads();
                 // 3. this pair's entries of the round, in supersample order:
@@ -1387,8 +1398,17 @@ __global__ void ssr_reduce_kernel(const float *part, int rows, int n_tiles, floa
 
 // ssr[row] = sum_t wt (y - flux)^2 over one flux row, in a fixed order;
 // row r observes passband r % n_b (rows are geometry-major, band-minor).
-__global__ void __launch_bounds__(256) ssr_rows_kernel(const float *flux, const float *y, const float *wt,
-                                                      int n_t, int n_b, float *ssr)
+// ssr_part_kernel: one CTA per (row, chunk of SSR_CHUNK times); every thread
+// loads its SSR_PER values before adding them, so a CTA keeps its whole chunk
+// in flight (a loop that waits on each load in turn is latency-bound), then a
+// fixed-order block sum.  ssr_reduce_kernel adds a row's chunk sums.
+constexpr int SSR_PER = 16;
+constexpr int SSR_CHUNK = 256 * SSR_PER;
+
+int ssr_chunks(int n_t) { return (n_t + SSR_CHUNK - 1) / SSR_CHUNK; }
+
+__global__ void __launch_bounds__(256) ssr_part_kernel(const float *flux, const float *y, const float *wt, int n_t,
+                                                      int n_b, float *part)
 {
     __shared__ float sred[8];
     const size_t row = blockIdx.x;
@@ -1396,13 +1416,35 @@ __global__ void __launch_bounds__(256) ssr_rows_kernel(const float *flux, const 
     const float *f = flux + row * n_t;
     const float *yb = y + (size_t)band * n_t;
     const float *wb = wt ? wt + (size_t)band * n_t : nullptr;
-    float s = 0.0f;
-    for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
-        float r = yb[t] - f[t];
-        s = fmaf(wb ? wb[t] : 1.0f, r * r, s);
+    const int t0 = blockIdx.y * SSR_CHUNK + threadIdx.x;
+    float fv[SSR_PER], yv[SSR_PER], wv[SSR_PER];
+#pragma unroll
+    for (int j = 0; j < SSR_PER; ++j) {
+        const int t = t0 + j * 256;
+        const bool ok = t < n_t;
+        fv[j] = ok ? f[t] : 0.0f;
+        yv[j] = ok ? yb[t] : 0.0f;
+        wv[j] = ok ? (wb ? wb[t] : 1.0f) : 0.0f;
     }
-    float tot = block_sum(s, sred);
-    if (threadIdx.x == 0) ssr[row] = tot;
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < SSR_PER; ++j) {
+        const float r = yv[j] - fv[j];
+        acc = fmaf(wv[j], r * r, acc);
+    }
+    const float tot = block_sum(acc, sred);
+    if (threadIdx.x == 0) part[row * gridDim.y + blockIdx.y] = tot;
+}
+
+int launch_ssr_rows(const float *flux, const float *y, const float *wt, int n_t, int n_b, size_t rows, float *part,
+                    float *ssr, cudaStream_t s)
+{
+    const int nc = ssr_chunks(n_t);
+    ssr_part_kernel<<<dim3((unsigned)rows, (unsigned)nc), 256, 0, s>>>(flux, y, wt, n_t, n_b, part);
+    int st = check_launch("ssr_part_kernel");
+    if (st) return st;
+    ssr_reduce_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(part, (int)rows, nc, ssr);
+    return check_launch("ssr_reduce_kernel");
 }
 
 // Interpolation-table nodes: the exact FP32 terms at (k_i, z_j), positions
@@ -1604,6 +1646,8 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
         off += align256((size_t)n_geom * n_t * sizeof(int));
         L.fscr = off;
         off += align256((size_t)n_v * n_b * n_t * sizeof(float));
+        L.part = off;   // residual chunk sums
+        off += align256((size_t)n_v * n_b * ssr_chunks(n_t) * sizeof(float));
         L.atab = off;
         off += align256((size_t)n_geom * n_zi * NP1 * sizeof(float));
         L.dtab = off;   // Chebyshev coefficient rows, padded to 16 bytes
@@ -2015,10 +2059,7 @@ static int ma_quad_list(const double *t, int n_t, const pt_orbit *orb, const flo
     ma_pairs_kernel<<<(unsigned)grid, MA_PPI, msm, s>>>(A);
     st = check_launch("ma_pairs_kernel");
     if (st) return st;
-    if (ssr) {
-        ssr_rows_kernel<<<orb->n_v * n_b, 256, 0, s>>>(A.flux, y, wt, n_t, n_b, ssr);
-        st = check_launch("ssr_rows_kernel");
-    }
+    if (ssr) st = launch_ssr_rows(A.flux, y, wt, n_t, n_b, (size_t)orb->n_v * n_b, (float *)(wb + L.part), ssr, s);
     return st;
 }
 
@@ -2363,10 +2404,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     else
         st = launch_cheb(A, T, plan->d_cx, plan->d_ccos, dtab, max_items, plan->ev0, plan->ev1, s);
     if (st) return st;
-    if (ssr) {
-        ssr_rows_kernel<<<orb->n_v * n_b, 256, 0, s>>>(A.flux, y, wt, n_t, n_b, ssr);
-        st = check_launch("ssr_rows_kernel");
-    }
+    if (ssr) st = launch_ssr_rows(A.flux, y, wt, n_t, n_b, (size_t)orb->n_v * n_b, (float *)(wb + L.part), ssr, s);
     return st;
 }
 
