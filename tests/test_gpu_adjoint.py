@@ -2,12 +2,16 @@
 oracle gradient, through the C ABI.
 
 Tolerance (derived from the FP32 error of the two factors of every term
-2 wt (f - y) df/dtheta): an absolute flux error eps_f = 1e-6 in f - y and a
-relative error eps_g in df/dtheta give
+2 wt (f - y) df/dtheta): an absolute flux error eps_f = 1e-6 in f - y (the
+exact path's flux tolerance) and a relative error eps_g in df/dtheta give
   |d grad_i| <= 2 sum_t wt |df/dtheta_i| (eps_f + eps_g |f - y|),
-with eps_g = 3e-4 (FP32 elliptic integrals and chain rule, cancellation in
-the conjunction-anchor terms near t0), plus 1e-5 of sum_t |2 wt (f-y) df/dtheta_i|
-for the FP32 accumulation.
+plus 1e-5 of sum_t |2 wt (f-y) df/dtheta_i| for the FP32 accumulation.
+eps_g = 1e-5 for every component (t0, P, a, b, e, w, k, u1, u2): FP32
+elliptic integrals and the chain rule through Kepler's equation.  Measured on
+these configurations the largest error is 0.11 of this bound (w) and below
+0.06 for every other component; the t0 gradient is a small difference of
+ingress and egress terms, so its error is judged against the size of its
+terms, not against the gradient itself.
 """
 import numpy as np
 import pytest
@@ -18,7 +22,7 @@ from paper_1504_07433_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 EPS_F = 1e-6
-EPS_G = 3e-4
+EPS_G = 1e-5
 
 
 @pytest.fixture(scope="module")
