@@ -627,135 +627,81 @@ __global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_ge
 // ---------------------------------------------------------------------------
 // Chebyshev form of the series.  For one geometry and order n,
 //   S_n(x) = sum_{j < n_j} T_{n,j} G_j(nu+2, 1; x)
-// is a polynomial of degree n_j - 1 in x, so it equals its interpolant at the
-// n_j Chebyshev nodes x_i = (1 + cos(pi (i + 1/2) / n_j)) / 2:
-//   S_n(x) = sum_{m < n_j} d_{n,m} T_m(2x - 1),
-//   d_{n,m} = (2 - [m = 0]) / n_j  sum_i cos(pi m (i + 1/2) / n_j) S_n(x_i)
-// (the discrete cosine transform of the node values; exact for a polynomial
-// of that degree).  The Chebyshev basis does not depend on n, so one
-// recurrence T_{m+1} = 2y T_m - T_{m-1} per supersample serves all N + 1
-// orders: N + 2 FMAs per term instead of 3 (N + 1).
-// gim_cheb_coef_kernel: node values by a Clenshaw summation of the Jacobi
-// series (FP32), then the transform with
-// compensated sums (each product and its FMA-exact error added by a two-sum).
+// is a polynomial of degree n_j - 1 in x, so it has an exact expansion
+//   S_n(x) = sum_{m < n_j} d_{n,m} T_m(y),   y = 2x - 1.
+// The Chebyshev basis does not depend on n, so one recurrence
+// T_{m+1} = 2y T_m - T_{m-1} per supersample serves all N + 1 orders:
+// N + 2 FMAs per term instead of 3 (N + 1).
+// gim_cheb_coef_kernel forms the d_{n,m} by Clenshaw's backward summation of
+// the Jacobi series (the recursion of Sec. 2.1.4, the table's r1_j, r2_j,
+// r3_{j+1}, T_{n,j}),
+//   b_j = T_j + (r1_j + r2_j x) b_{j+1} + r3_{j+1} b_{j+2},   S_n = b_0,
+// carried out on Chebyshev coefficient vectors instead of values: with
+// x = (1 + y)/2, multiplying by x is (1/2)(b + y b), and y T_m =
+// (T_{m+1} + T_{m-1})/2 (y T_0 = T_1), so (y b)_m = (b_{m-1} + b_{m+1})/2,
+// (y b)_0 = b_1 / 2, (y b)_1 = b_0 + b_2 / 2.  Each step touches every
+// coefficient once (about n_j^2 / 2 x 3 FMAs per order in all); in FP32 the
+// alpha_n it leads to stay within ~1e-7 of the FP64 series (emulated at
+// n_j = 192 over k = 0.05 .. 0.2), the level of the FP32 evaluation.
+// One warp per (geometry, order): lane l holds coefficients l S .. l S + S - 1
+// in registers, so a step needs the two neighbours across lanes only (two
+// shuffles); the table row sits in the warp's shared memory, read by
+// broadcast.  Warps for the row padding (orders N + 1 .. DS - 1) write zeros.
 // ---------------------------------------------------------------------------
-// One CTA per (geometry, pair of orders), so that enough warps hide the
-// dependent chains: the node values of the two orders, then their two
-// coefficient rows (one thread per m, cosine table through shared memory).
-// Orders past N (padding of the coefficient rows) get zeros.
-constexpr int CC_CI = 16;   // cosine-table rows per shared-memory chunk
-constexpr int CC_MR = 4;    // coefficient rows per thread: n_j <= CC_MR * 128
+constexpr int CW_WARPS = 4;   // warps per CTA of the coefficient kernel
 
-__global__ void __launch_bounds__(128) gim_cheb_coef_kernel(const float4 *gtab, int NP1, int n_j, int DS,
-                                                           const float *cx, const float *ccos, float *dtab)
+template <int S>
+__global__ void __launch_bounds__(32 * CW_WARPS) gim_cheb_coef_kernel(const float4 *gtab, int NP1, int n_j, int DS,
+                                                                     float *dtab)
 {
-    extern __shared__ __align__(16) unsigned char csm[];
+    extern __shared__ __align__(16) float4 ctab_sm[];   // [CW_WARPS][n_j]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x;
-    const int n0 = 2 * blockIdx.y;
-    const int no = min(2, max(0, NP1 - n0));   // orders of this CTA that exist
-    float4 *stab = reinterpret_cast<float4 *>(csm);     // [2][n_j]
-    float *sS = reinterpret_cast<float *>(stab + 2 * n_j);   // [n_j][2]
-    float *scos = sS + 2 * n_j;                          // [CC_CI][n_j]
-    if (no > 0) {
-        const float4 *src = gtab + ((size_t)g * NP1 + n0) * n_j;
-        for (int i = threadIdx.x; i < no * n_j; i += blockDim.x) stab[i] = src[i];
+    const int n = blockIdx.y * CW_WARPS + warp;
+    if (n >= DS) return;   // a whole warp; the kernel has no CTA-wide barrier
+    float *out = dtab + (size_t)g * n_j * DS + n;   // d_{n,m} at out[m DS]
+    if (n >= NP1) {
+        for (int m = lane; m < n_j; m += 32) out[(size_t)m * DS] = 0.0f;
+        return;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_j; i += blockDim.x) {
-        const float x = cx[i];
+    float4 *tab = ctab_sm + warp * n_j;
+    const float4 *src = gtab + ((size_t)g * NP1 + n) * n_j;
+    for (int j = lane; j < n_j; j += 32) tab[j] = src[j];
+    __syncwarp();
+    float b1[S], b2[S];
 #pragma unroll
-        for (int o = 0; o < 2; ++o) {
-            float c1 = 0.0f;
-            if (o < no) {
-                const float4 *tn = stab + o * n_j;
-                float c2 = 0.0f;
-#pragma unroll 4
-                for (int j = n_j - 1; j >= 0; --j) {
-                    float4 c = tn[j];
-                    float bj = fmaf(fmaf(c.y, x, c.x), c1, fmaf(c.z, c2, c.w));
-                    c2 = c1;
-                    c1 = bj;
-                }
-            }
-            sS[2 * i + o] = c1;
+    for (int s = 0; s < S; ++s) b1[s] = b2[s] = 0.0f;
+    const int m0 = lane * S;
+#pragma unroll 1
+    for (int j = n_j - 1; j >= 0; --j) {
+        const float4 c = tab[j];
+        const float a = fmaf(0.5f, c.y, c.x);   // the part of r1 + r2 x without y
+        const float h = 0.5f * c.y;             // the coefficient of y b
+        const float left = __shfl_up_sync(0xffffffffu, b1[S - 1], 1);   // b_{m0 - 1}
+        const float right = __shfl_down_sync(0xffffffffu, b1[0], 1);   // b_{m0 + S}
+        float nb[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float bl = (s == 0) ? (lane == 0 ? 0.0f : left) : b1[s - 1];
+            const float br = (s == S - 1) ? (lane == 31 ? 0.0f : right) : b1[s + 1];
+            if (m0 + s == 1) bl += bl;           // (y b)_1 = b_0 + b_2 / 2
+            const float yb = 0.5f * (bl + br);   // (y b)_0 = b_1 / 2: bl is 0 there
+            nb[s] = fmaf(a, b1[s], fmaf(h, yb, c.z * b2[s]));
         }
-    }
-    // cos(pi m (n_j - i - 1/2) / n_j) = (-1)^m cos(pi m (i + 1/2) / n_j): the
-    // transform needs the first ceil(n_j / 2) nodes only, applied to
-    // S_i + S_{n_j-1-i} for even m and S_i - S_{n_j-1-i} for odd m (for odd
-    // n_j the middle node pairs with itself; its cosine vanishes for odd m)
-    const int H = (n_j + 1) / 2;
-    float4 *sPM = reinterpret_cast<float4 *>(((uintptr_t)(scos + CC_CI * n_j) + 15) & ~(uintptr_t)15);
-    // sPM[H]: (S+ order 0, S+ order 1, S- order 0, S- order 1), 16-byte aligned
-    __syncthreads();
-    for (int i = threadIdx.x; i < H; i += blockDim.x) {
-        const int j = n_j - 1 - i;
-        float2 a = reinterpret_cast<const float2 *>(sS)[i];
-        float2 b = reinterpret_cast<const float2 *>(sS)[j];
-        sPM[i] = (i == j) ? make_float4(a.x, a.y, 0.0f, 0.0f)
-                          : make_float4(a.x + b.x, a.y + b.y, a.x - b.x, a.y - b.y);
-    }
-    float sum[CC_MR][2], err[CC_MR][2];
+        if (lane == 0) nb[0] += c.w;             // + T_j (degree 0)
 #pragma unroll
-    for (int r = 0; r < CC_MR; ++r) sum[r][0] = sum[r][1] = err[r][0] = err[r][1] = 0.0f;
-    if (no > 0) {
-        for (int i0 = 0; i0 < H; i0 += CC_CI) {
-            const int ci = min(CC_CI, H - i0);
-            __syncthreads();
-            if ((n_j & 3) == 0) {   // 128-bit copies, issued together
-                const float4 *cs4 = reinterpret_cast<const float4 *>(ccos + (size_t)i0 * n_j);
-                float4 *sc4 = reinterpret_cast<float4 *>(scos);
-                const int ne = ci * n_j / 4;
-#pragma unroll 4
-                for (int e = threadIdx.x; e < ne; e += blockDim.x) sc4[e] = cs4[e];
-            } else {
-#pragma unroll 4
-                for (int e = threadIdx.x; e < ci * n_j; e += blockDim.x) scos[e] = ccos[(size_t)i0 * n_j + e];
-            }
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < CC_MR; ++r) {
-                const int m = threadIdx.x + r * blockDim.x;
-                if (m >= n_j) break;
-                const bool odd = m & 1;
-                for (int ii = 0; ii < ci; ++ii) {
-                    const float a = scos[ii * n_j + m];
-                    const float4 pm = sPM[i0 + ii];
-                    const float2 v2 = odd ? make_float2(pm.z, pm.w) : make_float2(pm.x, pm.y);
-#pragma unroll
-                    for (int o = 0; o < 2; ++o) {
-                        const float v = o ? v2.y : v2.x;
-                        const float pr = a * v;
-                        const float pe = fmaf(a, v, -pr);
-                        const float ts = sum[r][o] + pr;
-                        const float bv = ts - sum[r][o];
-                        err[r][o] += ((sum[r][o] - (ts - bv)) + (pr - bv)) + pe;
-                        sum[r][o] = ts;
-                    }
-                }
-            }
+        for (int s = 0; s < S; ++s) {
+            b2[s] = b1[s];
+            b1[s] = nb[s];
         }
     }
 #pragma unroll
-    for (int r = 0; r < CC_MR; ++r) {
-        const int m = threadIdx.x + r * blockDim.x;
-        if (m >= n_j) break;
-        float2 o2 = make_float2(no > 0 ? sum[r][0] + err[r][0] : 0.0f, no > 1 ? sum[r][1] + err[r][1] : 0.0f);
-        float *row = dtab + ((size_t)g * n_j + m) * DS;
-        reinterpret_cast<float2 *>(row)[blockIdx.y] = o2;
-        // the last CTA of the geometry also clears the row's padding
-        if (blockIdx.y == gridDim.y - 1)
-            for (int q = 2 * (blockIdx.y + 1); q < DS; ++q) row[q] = 0.0f;
-    }
+    for (int s = 0; s < S; ++s)
+        if (m0 + s < n_j) out[(size_t)(m0 + s) * DS] = b1[s];
 }
 
-size_t gim_cheb_coef_smem(int n_j)
-{
-    // two orders' table rows and node values, a chunk of the cosine table,
-    // and the symmetric and antisymmetric node sums
-    return (size_t)n_j * (2 * sizeof(float4) + 2 * sizeof(float) + CC_CI * sizeof(float)) +
-           (size_t)((n_j + 1) / 2) * sizeof(float4) + 16;
-}
+// coefficients per lane of the coefficient kernel for a series depth
+int gim_cheb_coef_s(int n_j) { return (n_j + 31) / 32; }
 
 // Evaluation over the pair lists.  Persistent CTAs take items of GS_THREADS
 // listed pairs of one geometry and stage its coefficient rows once per item.
@@ -1680,8 +1626,6 @@ struct pt_gim_plan_s {
     float4 *d_coef;   // [N+1][n_j]: recursion of G_j(nu+2, 1; x), FP32
     double *d_A;      // [N+1][n_j]: A_{n,j}, FP64
     double *d_recb;   // [N+1][n_j][3]: recursion of G_j(nu+2, nu+1; x), FP64
-    float *d_cx;      // [n_j]: Chebyshev nodes in x, (1 + cos(pi (i + 1/2) / n_j)) / 2
-    float *d_ccos;    // [n_j (i)][n_j (m)]: (2 / n_j) cos(pi m (i + 1/2) / n_j), column m = 0 halved
     cudaEvent_t ev0, ev1;   // recorded around the series evaluation kernel when set (profiling)
 };
 
@@ -1739,23 +1683,24 @@ int launch_zi(const GimArgs &A, const float *atab, int n_in, int n_edge, size_t 
 }
 
 template <int NP1>
-int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab,
-                  size_t max_items, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s)
+int launch_cheb_t(const GimArgs &A, const float4 *T, float *dtab, size_t max_items, cudaEvent_t ev0, cudaEvent_t ev1,
+                  cudaStream_t s)
 {
-    // coefficients: one CTA per (geometry, pair of orders), every row of
-    // DS floats written (orders past N as zeros)
+    // coefficients: one warp per (geometry, order), rows padded to DS
+    // floats (the warps past order N write the padding zeros)
     constexpr int DS = (NP1 + 3) & ~3;
-    const size_t csm = gim_cheb_coef_smem(A.n_j);
-    static thread_local size_t csm_configured = 0;
-    if (csm > 48 * 1024 && csm > csm_configured) {
-        cudaError_t e = cudaFuncSetAttribute(gim_cheb_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)csm);
-        if (e != cudaSuccess) return set_cuda_error(e, "gim_cheb_coef_kernel smem attribute");
-        csm_configured = csm;
-    }
-    // one CTA per pair of existing orders: (N + 2) / 2 per geometry (with
-    // 256 geometries and N = 8 the grid fits one wave of the GPU)
-    gim_cheb_coef_kernel<<<dim3(A.n_geom, (A.N + 2) / 2), 128, csm, s>>>(T, A.N + 1, A.n_j, DS, cx, ccos, dtab);
+    const size_t csm = (size_t)CW_WARPS * A.n_j * sizeof(float4);
+    const dim3 cgrid(A.n_geom, (DS + CW_WARPS - 1) / CW_WARPS);
+    const int S = gim_cheb_coef_s(A.n_j);
+#define PT_COEF_LAUNCH(SV)                                                                                          \
+    gim_cheb_coef_kernel<SV><<<cgrid, 32 * CW_WARPS, csm, s>>>(T, A.N + 1, A.n_j, DS, dtab)
+    if (S <= 2) PT_COEF_LAUNCH(2);
+    else if (S <= 4) PT_COEF_LAUNCH(4);
+    else if (S <= 6) PT_COEF_LAUNCH(6);
+    else if (S <= 8) PT_COEF_LAUNCH(8);
+    else if (S <= 12) PT_COEF_LAUNCH(12);
+    else PT_COEF_LAUNCH(16);
+#undef PT_COEF_LAUNCH
     int st = check_launch("gim_cheb_coef_kernel");
     if (st) return st;
     // evaluation: persistent
@@ -1786,26 +1731,26 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, const float *cx, const floa
 }
 
 // Chebyshev path: coefficient and evaluation kernels, for N + 1 orders.
-int launch_cheb(const GimArgs &A, const float4 *T, const float *cx, const float *ccos, float *dtab, size_t max_items,
-                cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s)
+int launch_cheb(const GimArgs &A, const float4 *T, float *dtab, size_t max_items, cudaEvent_t ev0, cudaEvent_t ev1,
+                cudaStream_t s)
 {
     switch (A.N + 1) {
-    case 2: return launch_cheb_t<2>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 3: return launch_cheb_t<3>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 4: return launch_cheb_t<4>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 5: return launch_cheb_t<5>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 6: return launch_cheb_t<6>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 7: return launch_cheb_t<7>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 8: return launch_cheb_t<8>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 9: return launch_cheb_t<9>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 10: return launch_cheb_t<10>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 11: return launch_cheb_t<11>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 12: return launch_cheb_t<12>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 13: return launch_cheb_t<13>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 14: return launch_cheb_t<14>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 15: return launch_cheb_t<15>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    case 16: return launch_cheb_t<16>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
-    default: return launch_cheb_t<17>(A, T, cx, ccos, dtab, max_items, ev0, ev1, s);
+    case 2: return launch_cheb_t<2>(A, T, dtab, max_items, ev0, ev1, s);
+    case 3: return launch_cheb_t<3>(A, T, dtab, max_items, ev0, ev1, s);
+    case 4: return launch_cheb_t<4>(A, T, dtab, max_items, ev0, ev1, s);
+    case 5: return launch_cheb_t<5>(A, T, dtab, max_items, ev0, ev1, s);
+    case 6: return launch_cheb_t<6>(A, T, dtab, max_items, ev0, ev1, s);
+    case 7: return launch_cheb_t<7>(A, T, dtab, max_items, ev0, ev1, s);
+    case 8: return launch_cheb_t<8>(A, T, dtab, max_items, ev0, ev1, s);
+    case 9: return launch_cheb_t<9>(A, T, dtab, max_items, ev0, ev1, s);
+    case 10: return launch_cheb_t<10>(A, T, dtab, max_items, ev0, ev1, s);
+    case 11: return launch_cheb_t<11>(A, T, dtab, max_items, ev0, ev1, s);
+    case 12: return launch_cheb_t<12>(A, T, dtab, max_items, ev0, ev1, s);
+    case 13: return launch_cheb_t<13>(A, T, dtab, max_items, ev0, ev1, s);
+    case 14: return launch_cheb_t<14>(A, T, dtab, max_items, ev0, ev1, s);
+    case 15: return launch_cheb_t<15>(A, T, dtab, max_items, ev0, ev1, s);
+    case 16: return launch_cheb_t<16>(A, T, dtab, max_items, ev0, ev1, s);
+    default: return launch_cheb_t<17>(A, T, dtab, max_items, ev0, ev1, s);
     }
 }
 
@@ -2223,22 +2168,12 @@ int pt_gim_plan_create(int N, int n_j, pt_gim_plan *out)
             for (int c = 0; c < 3; ++c) hrb[((size_t)n * n_j + j) * 3 + c] = r[c];
         }
     }
-    // Chebyshev nodes and the discrete cosine transform of the series-
-    // evaluation change of basis (FP64 here, stored FP32)
-    float *hcx = new float[n_j];
-    float *hcc = new float[(size_t)n_j * n_j];
-    for (int i = 0; i < n_j; ++i) hcx[i] = (float)(0.5 * (1.0 + cos(PI_D * (i + 0.5) / n_j)));
-    for (int m = 0; m < n_j; ++m)
-        for (int i = 0; i < n_j; ++i)
-            hcc[(size_t)i * n_j + m] = (float)((m == 0 ? 1.0 : 2.0) / n_j * cos(PI_D * m * (i + 0.5) / n_j));
     pt_gim_plan p = new pt_gim_plan_s;
     p->N = N;
     p->n_j = n_j;
     p->d_coef = nullptr;
     p->d_A = nullptr;
     p->d_recb = nullptr;
-    p->d_cx = nullptr;
-    p->d_ccos = nullptr;
     p->ev0 = p->ev1 = nullptr;
     cudaError_t e = cudaMalloc(&p->d_coef, cnt * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_A, cnt * sizeof(double));
@@ -2246,22 +2181,13 @@ int pt_gim_plan_create(int N, int n_j, pt_gim_plan *out)
     if (e == cudaSuccess) e = cudaMemcpy(p->d_coef, hcoef, cnt * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_A, hA, cnt * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_recb, hrb, cnt * 3 * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_cx, n_j * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_ccos, (size_t)n_j * n_j * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_cx, hcx, n_j * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(p->d_ccos, hcc, (size_t)n_j * n_j * sizeof(float), cudaMemcpyHostToDevice);
     delete[] hcoef;
     delete[] hA;
     delete[] hrb;
-    delete[] hcx;
-    delete[] hcc;
     if (e != cudaSuccess) {
         cudaFree(p->d_coef);
         cudaFree(p->d_A);
         cudaFree(p->d_recb);
-        cudaFree(p->d_cx);
-        cudaFree(p->d_ccos);
         delete p;
         return set_cuda_error(e, "pt_gim_plan_create");
     }
@@ -2283,8 +2209,6 @@ int pt_gim_plan_destroy(pt_gim_plan p)
     cudaFree(p->d_coef);
     cudaFree(p->d_A);
     cudaFree(p->d_recb);
-    cudaFree(p->d_cx);
-    cudaFree(p->d_ccos);
     delete p;
     return PT_OK;
 }
@@ -2402,7 +2326,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     if (zi)
         st = launch_zi(A, atab, n_in, n_edge, smem, max_items, s);
     else
-        st = launch_cheb(A, T, plan->d_cx, plan->d_ccos, dtab, max_items, plan->ev0, plan->ev1, s);
+        st = launch_cheb(A, T, dtab, max_items, plan->ev0, plan->ev1, s);
     if (st) return st;
     if (ssr) st = launch_ssr_rows(A.flux, y, wt, n_t, n_b, (size_t)orb->n_v * n_b, (float *)(wb + L.part), ssr, s);
     return st;
