@@ -669,31 +669,39 @@ __global__ void __launch_bounds__(32 * CW_WARPS) gim_cheb_coef_kernel(const floa
     for (int j = lane; j < n_j; j += 32) tab[j] = src[j];
     __syncwarp();
     float b1[S], b2[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) b1[s] = b2[s] = 0.0f;
+    float wl[S];   // weight of the lower neighbour in (y b)_m: 1/2, 1 at m = 1, 0 at m = 0
     const int m0 = lane * S;
-#pragma unroll 1
-    for (int j = n_j - 1; j >= 0; --j) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        b1[s] = b2[s] = 0.0f;
+        wl[s] = (m0 + s == 0) ? 0.0f : (m0 + s == 1 ? 1.0f : 0.5f);
+    }
+    // one step: from (bn = b_{j+1}, bo = b_{j+2}) to b_j, written over bo
+    auto step = [&](int j, float (&bn)[S], float (&bo)[S]) {
         const float4 c = tab[j];
         const float a = fmaf(0.5f, c.y, c.x);   // the part of r1 + r2 x without y
         const float h = 0.5f * c.y;             // the coefficient of y b
-        const float left = __shfl_up_sync(0xffffffffu, b1[S - 1], 1);   // b_{m0 - 1}
-        const float right = __shfl_down_sync(0xffffffffu, b1[0], 1);   // b_{m0 + S}
-        float nb[S];
+        const float left = __shfl_up_sync(0xffffffffu, bn[S - 1], 1);   // b_{m0 - 1}
+        const float right = __shfl_down_sync(0xffffffffu, bn[0], 1);   // b_{m0 + S}
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            float bl = (s == 0) ? (lane == 0 ? 0.0f : left) : b1[s - 1];
-            const float br = (s == S - 1) ? (lane == 31 ? 0.0f : right) : b1[s + 1];
-            if (m0 + s == 1) bl += bl;           // (y b)_1 = b_0 + b_2 / 2
-            const float yb = 0.5f * (bl + br);   // (y b)_0 = b_1 / 2: bl is 0 there
-            nb[s] = fmaf(a, b1[s], fmaf(h, yb, c.z * b2[s]));
+            const float bl = (s == 0) ? left : bn[s - 1];
+            const float br = (s == S - 1) ? (lane == 31 ? 0.0f : right) : bn[s + 1];
+            const float yb = fmaf(wl[s], bl, 0.5f * br);
+            bo[s] = fmaf(a, bn[s], fmaf(h, yb, c.z * bo[s]));
         }
-        if (lane == 0) nb[0] += c.w;             // + T_j (degree 0)
+        if (lane == 0) bo[0] += c.w;             // + T_j (degree 0)
+    };
+    int j = n_j - 1;
+#pragma unroll 1
+    for (; j >= 1; j -= 2) {
+        step(j, b1, b2);       // b_j into b2
+        step(j - 1, b2, b1);   // b_{j-1} into b1
+    }
+    if (j == 0) {
+        step(0, b1, b2);
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            b2[s] = b1[s];
-            b1[s] = nb[s];
-        }
+        for (int s = 0; s < S; ++s) b1[s] = b2[s];
     }
 #pragma unroll
     for (int s = 0; s < S; ++s)
