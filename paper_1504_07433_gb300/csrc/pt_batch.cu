@@ -194,8 +194,17 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
                 fbuf[b * TT + tl] = 1.0f - swt[4 * b + 3] * dep;
             }
         }
+        // unit u = b nq + qi; the thread's units advance by TT = dq nq + dr
+        const int dq = nq > 0 ? TT / nq : 0, dr = nq > 0 ? TT - dq * nq : 0;
+        int ub = nq > 0 ? tid / nq : 0, uq = tid - ub * nq;
         for (int u = A.khat ? nu : tid; u < nu; u += TT) {
-            int b = u / nq, qi = u - b * nq;
+            const int b = ub, qi = uq;
+            ub += dq;
+            uq += dr;
+            if (uq >= nq) {
+                uq -= nq;
+                ++ub;
+            }
             int tl = squeue[qi];
             float kb = swt[4 * b + 3];
             float le, ld, ed;
