@@ -99,7 +99,8 @@ __device__ __forceinline__ float s2c2_int(float m, float K, float E)
 // Overlap integrals I (x pi-free form: I_1 = pi le, I_mu = pi ld', I_mu2 =
 // pi (le - ed)) and their derivatives d[0..5] = dI_1/dk, dI_1/dz, dI_mu/dk,
 // dI_mu/dz, dI_mu2/dk, dI_mu2/dz.
-__device__ __forceinline__ void overlap_derivs(float p, float z, float *d)
+__device__ __forceinline__ void overlap_derivs(float p, float z, float *d, bool have_ke = false, float Kin = 0.0f,
+                                               float Ein = 0.0f)
 {
     for (int i = 0; i < 6; ++i) d[i] = 0.0f;
     if (!(z < 1.0f + p) || !(p > 0.0f)) return;
@@ -110,8 +111,8 @@ __device__ __forceinline__ void overlap_derivs(float p, float z, float *d)
     if (dd < 0.0f) {                                   // full circle inside the star
         float m = 4.0f * z * p / oma;
         float kc = sqrtf(-dd * (1.0f + z + p) / oma);
-        float K, E;
-        ellke(kc, &K, &E);
+        float K = Kin, E = Ein;
+        if (!have_ke) ellke(kc, &K, &E);
         float so = sqrtf(oma);
         d[0] = 2.0f * PI_F * p;
         d[2] = 4.0f * p * so * E;
@@ -131,7 +132,12 @@ __device__ __forceinline__ void overlap_derivs(float p, float z, float *d)
         E = 1.0f;
         mcK = 0.0f;
     } else {
-        ellke(sqrtf(mc1), &K, &E);
+        if (have_ke) {
+            K = Kin;
+            E = Ein;
+        } else {
+            ellke(sqrtf(mc1), &K, &E);
+        }
         mcK = mc1 * K;
     }
     float icos = -2.0f * sk, icos2 = kap0 + sk * ck;
@@ -281,8 +287,9 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
     if (V <= 0.0f) return 1.0f;
     float Vi = V * c.ci;
     float z = sqrtf(fmaf(U, U, Vi * Vi));
-    float le, ld, ed;
-    pt::ma_terms(c.k, z, &le, &ld, &ed);
+    float le, ld, ed, Kc = 0.0f, Ec = 0.0f;
+    bool have_ke = false;
+    pt::ma_terms<true>(c.k, z, &le, &ld, &ed, &Kc, &Ec, &have_ke);
     if (le == 0.0f && ld == 0.0f && ed == 0.0f) return 1.0f;
     const float pi = PI_F;
     float I0 = pi * le, I1 = pi * ld, I2 = pi * (le - ed);
@@ -290,7 +297,7 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
     float invPD = 1.0f / (pi * c.D);
     float f = 1.0f - N * invPD;
     float d[6];
-    overlap_derivs(c.k, z, d);
+    overlap_derivs(c.k, z, d, have_ke, Kc, Ec);
     float dFdk = -(c.c0 * d[0] + c.c2 * d[2] - c.u2 * d[4]) * invPD;
     float dFdz = -(c.c0 * d[1] + c.c2 * d[3] - c.u2 * d[5]) * invPD;
     g[6] = dFdk;

@@ -236,6 +236,45 @@ __device__ __forceinline__ void cel2(float kc, float a1, float b1, float rho, fl
     *r2 = __fdividef((0.5f * PT_PI_F) * fmaf(a2, m, b2), m * (m + p2));
 }
 
+// cel2's loop carrying K = cel(kc, 1, 1, 1) and E = cel(kc, 1, 1, kc^2) in place
+// of one combination of them (cel with p = 1 is linear in (a, b), so
+// cel(kc, 1, cK + cE, cK + cE kc^2) = cK K + cE E), for callers that also need
+// K and E themselves.
+__device__ __forceinline__ void cel3(float kc, float rho, float a2, float *K, float *E, float *r2)
+{
+    float p1 = 1.0f;
+    float p2 = fast_sqrt(rho);
+    float aK = 1.0f, bK = 1.0f, aE = 1.0f, bE = kc * kc, b2 = 0.0f;
+    float m = 1.0f, e = kc;
+#pragma unroll 1
+    for (int it = 0; it < 10; ++it) {
+        float ip1 = __fdividef(1.0f, p1);
+        float ip2 = __fdividef(1.0f, p2);
+        float g = e * ip1;
+        float f = aK;
+        aK = fmaf(bK, ip1, aK);
+        bK = 2.0f * fmaf(f, g, bK);
+        f = aE;
+        aE = fmaf(bE, ip1, aE);
+        bE = 2.0f * fmaf(f, g, bE);
+        p1 += g;
+        f = a2;
+        a2 = fmaf(b2, ip2, a2);
+        g = e * ip2;
+        b2 = 2.0f * fmaf(f, g, b2);
+        p2 += g;
+        g = m;
+        m = kc + m;
+        if (fabsf(g - kc) <= g * 3e-4f) break;
+        kc = 2.0f * fast_sqrt(e);
+        e = kc * m;
+    }
+    const float den = __fdividef(0.5f * PT_PI_F, m * (m + p1));
+    *K = fmaf(aK, m, bK) * den;
+    *E = fmaf(aE, m, bE) * den;
+    *r2 = __fdividef((0.5f * PT_PI_F) * fmaf(a2, m, b2), m * (m + p2));
+}
+
 // ---------------------------------------------------------------------------
 // Mandel & Agol (2002) terms for the quadratic law, FP32.
 //   le = lambda_e, ld = lambda_d + 2/3 Theta(p - z), ed = eta_d.
@@ -261,8 +300,14 @@ __device__ __forceinline__ void cel2(float kc, float a1, float b1, float rho, fl
 // cannot evaluate (z = 1 - p, z = p, p = z = 1/2, star covered) are taken
 // separately; near them the general formulas stay accurate in FP32.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld, float *ed)
+// With KE, K and E of the general cases' modulus (cases 2, 3, 8, 9: the
+// partial and inside overlaps) come back too, *have_ke = true; other cases
+// leave *have_ke false.
+template <bool KE = false>
+__device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld, float *ed, float *Kout = nullptr,
+                                         float *Eout = nullptr, bool *have_ke = nullptr)
 {
+    if (KE) *have_ke = false;
     *le = 0.0f;
     *ld = 0.0f;
     *ed = 0.0f;
@@ -345,7 +390,16 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
     float lam = cst;
     if (need_cel) {
         float r1, r2;
-        cel2(kc, cKp + cE, fmaf(cE, kc * kc, cKp), rho, cR, &r1, &r2);
+        if (KE && d != 0.0f && zmp != 0.0f) {
+            float K, E;
+            cel3(kc, rho, cR, &K, &E, &r2);
+            r1 = fmaf(cKp, K, cE * E);
+            *Kout = K;
+            *Eout = E;
+            *have_ke = true;
+        } else {
+            cel2(kc, cKp + cE, fmaf(cE, kc * kc, cKp), rho, cR, &r1, &r2);
+        }
         lam = fmaf(pref, r1 + r2, cst);
     }
     if (p > z) lam += 2.0f / 3.0f;
