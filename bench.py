@@ -461,6 +461,19 @@ def run_oracle_step(wl, n_v, n_t=None, n_threads=0):
     return dt, fm.size + fg.size, (fm, fg)
 
 
+def _rate(fn, n_points, min_s=0.3):
+    """Oracle points per second of `fn` (which computes `n_points` points per call),
+    repeating the call until `min_s` seconds have passed; returns (last result, rate)."""
+    t0 = time.perf_counter()
+    calls = 0
+    while True:
+        out = fn()
+        calls += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_s:
+            return out, n_points * calls / dt
+
+
 def _maxerr(a, b):
     return float(np.max(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))))
 
@@ -483,6 +496,10 @@ def cpu_leg(wl, n_v, n_t, n_ss, head, legs):
                      % (nv, n_v, n_t, n_ss, N_LD, N_J, dt),
            "value_1_thread": p1 / dt1,
            "sample_1_thread": "%d vectors, same times, one thread: %.1f s" % (n1, dt1)}
+    # oracle rates per workload: all host cores and one thread, each on the leg's own check sample
+    per = {"long_cadence": {"value": p / dt, "value_1_thread": p1 / dt1,
+                            "unit": "flux points/s (MA + Gimenez N=8)"}}
+    cpu["per_workload"] = per
     errs = {"headline": {"ma": _maxerr(head["fm"], rm[:, 0]), "gimenez": _maxerr(head["fg"], rg[:, 0]),
                          "sample": "first %d vectors, every time" % nv}}
     if "e2e_ssr" in legs:
@@ -496,7 +513,10 @@ def cpu_leg(wl, n_v, n_t, n_ss, head, legs):
     if "plain" in legs:
         L = legs["plain"]
         t, orb, k, ld, _ = _oracle_sample(L["wl"], 1)
-        ref, _ = oracle.lc_ma(t, orb, k, ld)
+        (ref, _), r_all = _rate(lambda: oracle.lc_ma(t, orb, k, ld), len(t))
+        _, r_one = _rate(lambda: oracle.lc_ma(t, orb, k, ld, n_threads=1), len(t))
+        per["plain"] = {"value": r_all, "value_1_thread": r_one, "unit": "flux points/s (MA)",
+                        "sample": "all %d times" % len(t)}
         errs["plain"] = {"ma": _maxerr(L["flux"], ref), "sample": "every point"}
     if "ma_interp" in legs:
         L = legs["ma_interp"]
@@ -523,7 +543,13 @@ def cpu_leg(wl, n_v, n_t, n_ss, head, legs):
         names = ("t0", "P", "a", "b", "e", "w", "k", "u1", "u2")
         rows = np.stack([np.asarray(th[nm])[L["idx"]].astype(np.float64) if nm in ("t0", "P")
                          else f32(np.asarray(th[nm])[L["idx"]]) for nm in names], axis=1)
-        ssr_r, grad_r = oracle.ssr_grad(L["wl"]["t"], rows, f32(L["y"]))
+        n_pts = rows.shape[0] * len(L["wl"]["t"])
+        (ssr_r, grad_r), r_all = _rate(lambda: oracle.ssr_grad(L["wl"]["t"], rows, f32(L["y"])), n_pts)
+        _, r_one = _rate(lambda: oracle.ssr_grad(L["wl"]["t"], rows[:1], f32(L["y"]), n_threads=1),
+                         len(L["wl"]["t"]))
+        per["adjoint"] = {"value": r_all, "value_1_thread": r_one,
+                          "unit": "flux points/s (residual sum + 9-component gradient)",
+                          "sample": "%d vectors x %d times (one thread: 1 vector)" % (rows.shape[0], len(L["wl"]["t"]))}
         rel = np.abs(L["grad"] - grad_r) / np.maximum(np.abs(grad_r), 1e-30)
         # the scale of the sum: sum_t |2 (f - y) df/dtheta_i| (the gradient of t0 is a small
         # difference of ingress and egress terms, so |grad| alone overstates its error)
@@ -547,8 +573,16 @@ def cpu_leg(wl, n_v, n_t, n_ss, head, legs):
         o = bw["orbit"]
         orb = dict(t0=np.asarray(o["t0"])[pairs[:, 0]], P=np.asarray(o["P"])[pairs[:, 0]],
                    a=f32(o["a"])[pairs[:, 0]], inc=f32(o["inc"])[pairs[:, 0]])
-        ref, _ = oracle.lc_ma(bw["t"], orb, f32(bw["k"])[pairs[:, 0], pairs[:, 1]][:, None],
-                              f32(bw["ld"])[pairs[:, 0], pairs[:, 1]][:, None, :])
+        kp = f32(bw["k"])[pairs[:, 0], pairs[:, 1]][:, None]
+        ldp = f32(bw["ld"])[pairs[:, 0], pairs[:, 1]][:, None, :]
+        n_pts = len(pairs) * len(bw["t"])
+        (ref, _), r_all = _rate(lambda: oracle.lc_ma(bw["t"], orb, kp, ldp), n_pts)
+        o1 = {key: val[:1] for key, val in orb.items()}
+        _, r_one = _rate(lambda: oracle.lc_ma(bw["t"], o1, kp[:1], ldp[:1], n_threads=1), len(bw["t"]))
+        per["batched"] = {"value": r_all, "value_1_thread": r_one,
+                          "unit": "flux points/s (MA, per-passband k)",
+                          "sample": "%d (walker, passband) light curves x %d times (one thread: 1)"
+                                    % (len(pairs), len(bw["t"]))}
         yy = f32(bw["y"])[pairs[:, 1]]
         ssr_ref = np.sum((yy - ref[:, 0]) ** 2, axis=1)
         e = {"ssr_max_rel": float(np.max(np.abs(L["ssr"] - ssr_ref) / ssr_ref)),
@@ -569,7 +603,12 @@ def cpu_leg(wl, n_v, n_t, n_ss, head, legs):
     if "surrogate" in legs:
         L = legs["surrogate"]
         kk, zz = L["k"].astype(np.float64), L["z"].astype(np.float64)
-        ref = oracle.ma_terms_batch(kk, zz)
+        ref, r_all = _rate(lambda: oracle.ma_terms_batch(kk, zz), len(kk))
+        n1 = min(len(kk), 100_000)
+        _, r_one = _rate(lambda: oracle.ma_terms_batch(kk[:n1], zz[:n1], n_threads=1), n1)
+        per["surrogate_domain"] = {"value": r_all, "value_1_thread": r_one,
+                                   "unit": "(k, z) points/s (lambda_e, lambda_d, eta_d)",
+                                   "sample": "%d points (one thread: %d)" % (len(kk), n1)}
         ref[:, 1] += np.where(kk > zz, 2.0 / 3.0, 0.0)
 
         def bound(terms, mask=None):
