@@ -59,7 +59,7 @@ enum {
     PT_ERR_DOMAIN = 2,        /* parameter outside the supported domain (host check or pt_status_read) */
     PT_ERR_NOT_CONVERGED = 3, /* Newton step cap hit (pt_status_read of an n_bad counter) */
     PT_ERR_CUDA = 4,          /* kernel launch or CUDA runtime error */
-    PT_ERR_WORKSPACE = 5      /* work buffer null or smaller than required */
+    PT_ERR_WORKSPACE = 5      /* work buffer null, misaligned or smaller than required */
 };
 
 #define PT_Z_BEHIND 1.0e30f
@@ -167,7 +167,9 @@ int pt_ma_terms(const float *k_dev, const float *z_dev, size_t n, float *lam_e_d
  *              for unit weights); needed only when ssr_dev != NULL
  *   flux_dev   [n_v][n_b][n_t] output flux cube, or NULL
  *   ssr_dev    [n_v][n_b] output sum_t wt (y - f)^2, or NULL
- *   work_dev   device scratch of at least pt_ma_quad_work_bytes() bytes
+ *   work_dev   device scratch of at least pt_ma_quad_work_bytes() bytes,
+ *              16-byte aligned (as cudaMalloc and PyTorch allocations are;
+ *              the kernels read it in 16-byte vectors)
  *   n_bad_dev  optional device int: points whose Newton iteration hit
  *              max_iter are added to it
  * With k_per_band == 0 one geometry pass serves all n_b limb-darkening sets

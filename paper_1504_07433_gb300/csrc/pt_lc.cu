@@ -1918,7 +1918,7 @@ static int lc_common_check(const double *t, int n_t, const pt_orbit *orb, const 
     if (!flux && !ssr) return PT_ERR_ARG;
     if (!t || !k || !ld) return PT_ERR_ARG;
     if (ssr && !y) return PT_ERR_ARG;
-    if (!work) return PT_ERR_WORKSPACE;
+    if (!work || ((uintptr_t)work & 15u)) return PT_ERR_WORKSPACE;
     return PT_OK;
 }
 

@@ -269,3 +269,70 @@ def test_evaluation_timing_events(torch_cuda):
     assert torch.equal(f0, f2)
     with pytest.raises(pt.PTError):
         plan.time_evaluation(e0, None)
+
+
+def test_graph_capture_and_workspace_reuse(torch_cuda):
+    """A call captured into a CUDA graph and replayed, and back-to-back calls
+    with two radius-ratio sets that reuse one workspace on a non-default
+    stream, give the flux of a plain call, which matches the oracle."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=6, n_t=3000)
+    wl["ld"] = wl["ld_gim"]
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(8, 96)
+    n_v, n_t = k.numel(), t.numel()
+    work = torch.empty(plan.work_bytes(n_t, n_v, 1), dtype=torch.uint8, device="cuda")
+    f0, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=work)
+    torch.cuda.synchronize()
+    ref = _oracle_lc(wl, 96)
+    assert np.max(np.abs(f0.cpu().numpy() - ref)) <= TOL
+    # two radius-ratio sets through one workspace, back to back on another stream
+    k2 = (k * 1.05).contiguous()
+    s = torch.cuda.Stream()
+    fa = torch.empty_like(f0)
+    fb = torch.empty_like(f0)
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            pt.gimenez(plan, t, orb, k2, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=work, flux=fa)
+            pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=work, flux=fb)
+    torch.cuda.synchronize()
+    assert torch.equal(fb, f0)
+    fa_ref, _ = pt.gimenez(plan, t, orb, k2, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+    torch.cuda.synchronize()
+    assert torch.equal(fa, fa_ref)
+    # captured into a graph and replayed
+    fg = torch.empty_like(f0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=work, flux=fg)
+    torch.cuda.synchronize()
+    fg.zero_()
+    with torch.cuda.graph(g, stream=s):
+        pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=work, flux=fg)
+    fg.zero_()
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(fg, f0)
+    plan.close()
+
+
+def test_misaligned_workspace_rejected(torch_cuda):
+    """A work buffer that does not start on a 16-byte boundary is refused
+    (PT_ERR_WORKSPACE) before any kernel is launched."""
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=2, n_t=500)
+    wl["ld"] = wl["ld_gim"]
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(8, 64)
+    need = plan.work_bytes(t.numel(), 2, 1)
+    raw = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pt.PTError):
+        pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=raw[4:])
+    f, _ = pt.gimenez(plan, t, orb, k, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=raw[16:])
+    torch.cuda.synchronize()
+    assert torch.isfinite(f).all()
+    plan.close()
