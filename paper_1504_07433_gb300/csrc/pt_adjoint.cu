@@ -386,8 +386,18 @@ __global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
     for (int i = 0; i < 10; ++i) acc[i] = 0.0f;
     bool bad = false;
     const float inv_ss = 1.0f / (float)A.n_ss;
+    // the next time's inputs are loaded one iteration ahead
+    float2 ts_n = threadIdx.x < A.n_t ? A.tsplit[threadIdx.x] : make_float2(0.0f, 0.0f);
+    float y_n = threadIdx.x < A.n_t ? A.y[threadIdx.x] : 0.0f;
+    float w_n = (A.wt && threadIdx.x < A.n_t) ? A.wt[threadIdx.x] : 1.0f;
     for (int i = threadIdx.x; i < A.n_t; i += TB) {
-        float2 ts = A.tsplit[i];
+        const float2 ts = ts_n;
+        const float yi = y_n, wi = w_n;
+        if (i + TB < A.n_t) {
+            ts_n = A.tsplit[i + TB];
+            y_n = A.y[i + TB];
+            w_n = A.wt ? A.wt[i + TB] : 1.0f;
+        }
         // epoch and offset (double-float phase reduction)
         float s = ts.x - c.g.t0h;
         float n_ep = rintf(s * c.g.invP);
@@ -415,8 +425,7 @@ __global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
             for (int j = 0; j < 9; ++j) gp[j] *= inv_ss;
         }
         if (A.flux) A.flux[(size_t)v * A.n_t + i] = f;
-        float wi = A.wt ? A.wt[i] : 1.0f;
-        float res = f - A.y[i];
+        float res = f - yi;
         acc[9] = fmaf(wi * res, res, acc[9]);
         float tw = 2.0f * wi * res;
 #pragma unroll
