@@ -722,8 +722,10 @@ int gim_cheb_coef_s(int n_j) { return (n_j + 31) / 32; }
 //     consecutive entries, whatever pairs they belong to, so that no lane
 //     idles on an out-of-transit supersample: one Chebyshev recurrence per
 //     entry, T_{m+1} = 2y T_m - T_{m-1}, and one FMA per order n and m for
-//     d_{n,m} T_m (scalar FMAs: on this part they sustain more FMAs per
-//     cycle than the two-lane form).  Rounds of GS_GMAX = 4 entries per
+//     d_{n,m} T_m, two orders per two-lane FMA instruction (fma.rn.f32x2:
+//     a third fewer instructions than scalar FMAs, and measured on this
+//     part 0.68 of the FP32 peak in series multiply-adds against 0.52 for
+//     the scalar form of the same loop).  Rounds of GS_GMAX = 4 entries per
 //     thread while at least 4 GS_THREADS entries are left, then one round of
 //     the fewest entries per thread (1 to 3) that holds the rest (each
 //     coefficient load serves the thread's entries).  The S_n go to shared
@@ -733,6 +735,40 @@ int gim_cheb_coef_s(int n_j) { return (n_j + 31) / 32; }
 // After the last batch, the passband combination of Sec. 2.1.3.
 constexpr int GS_SSB = 16;    // supersamples per batch of the Chebyshev kernel
 constexpr int GS_GMAX = 4;    // entries per thread in the largest round
+constexpr int GS_WROWS = 8;   // passbands whose combination weights are staged per geometry
+
+// The geometry of work item it: the largest g with pref[g] <= it (pref is
+// non-decreasing, pref[0] = 0 <= it), found by one warp: each round splits
+// [lo, hi] into 32 strides and loads their first entries in parallel, the
+// lanes whose entry is <= it form a prefix, and its last lane brackets the
+// answer.  Two rounds (two dependent loads) up to 1,024 geometries.
+__device__ __forceinline__ int item_geometry(const int *pref, int n_geom, int it, int lane)
+{
+    int lo = 0, hi = n_geom - 1;
+    for (;;) {
+        const int step = (hi - lo + 32) / 32;   // ceil((hi - lo + 1) / 32)
+        const int idx = lo + lane * step;
+        const bool ok = idx <= hi && pref[idx] <= it;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        lo += (31 - __clz(m)) * step;
+        if (step == 1) return lo;
+        hi = min(hi, lo + step - 1);
+    }
+}
+
+// (a0, a1) += (d0, d1) w as one two-lane FMA (sm_100 and later).  Each lane
+// is a fused multiply-add rounded once, so the result is that of two fmaf.
+__device__ __forceinline__ void fma2_pair(float d0, float d1, float w, float &a0, float &a1)
+{
+    float2 a = make_float2(a0, a1);
+    const float2 d = make_float2(d0, d1);
+    const float2 ww = make_float2(w, w);
+    asm("fma.rn.f32x2 %0, %1, %2, %0;"
+        : "+l"(*reinterpret_cast<unsigned long long *>(&a))
+        : "l"(*reinterpret_cast<const unsigned long long *>(&d)), "l"(*reinterpret_cast<const unsigned long long *>(&ww)));
+    a0 = a.x;
+    a1 = a.y;
+}
 
 template <int NP1, int G>
 __device__ __forceinline__ void cheb_eval(const float *sd, int nj, const float (&y)[G], float (&acc)[G][NP1])
@@ -763,8 +799,12 @@ __device__ __forceinline__ void cheb_eval(const float *sd, int nj, const float (
 #pragma unroll
         for (int e = 0; e < G; ++e) {
             wn[e] = fmaf(a2[e], wp[e], -wn[e]);
+            // orders in pairs through the two-lane FMA (each lane one FMA,
+            // rounded once: the same result as two fmaf), the odd last order
+            // scalar
 #pragma unroll
-            for (int n = 0; n < NP1; ++n) acc[e][n] = fmaf(dm[n], wn[e], acc[e][n]);
+            for (int n = 0; n + 1 < NP1; n += 2) fma2_pair(dm[n], dm[n + 1], wn[e], acc[e][n], acc[e][n + 1]);
+            if (NP1 & 1) acc[e][NP1 - 1] = fmaf(dm[NP1 - 1], wn[e], acc[e][NP1 - 1]);
         }
     };
     int m = 2;
@@ -838,7 +878,8 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
     float *sS = sd + nj * DS;                                    // [NP1][CH] series values of a round
     float2 *syq = reinterpret_cast<float2 *>(sS + NP1 * CH);     // [ssb][GS_THREADS] (y, q) per pair
     __shared__ GeomRec srec;
-    __shared__ int sitem, sgeom, sbad;
+    __shared__ int sitem, sgeom, sfirst, scount, sbad;
+    __shared__ float swt[GS_WROWS][NP1 + 1];   // per passband: 1 - sum u, u_1..u_N, D
     __shared__ int sst[GS_THREADS + 1];   // first dense entry of each pair; sst[GS_THREADS] = entries
     __shared__ int swarp[GS_THREADS / 32];
     const int tid = threadIdx.x;
@@ -850,20 +891,20 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
     if (tid == 0) sbad = 0;
 #pragma unroll 1
     for (;;) {
-        if (tid == 0) {
-            int it = atomicAdd(A.ctr, 1);
+        if (warp == 0) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(A.ctr, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
             int g = -1;
-            if (it < total) {   // the largest g with pref[g] <= it
-                int lo = 0, hi = A.n_geom - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (A.pref[mid] <= it) lo = mid;
-                    else hi = mid - 1;
+            if (it < total) g = item_geometry(A.pref, A.n_geom, it, lane);
+            if (lane == 0) {
+                sitem = it;
+                sgeom = g;
+                if (g >= 0) {
+                    sfirst = A.pref[g];
+                    scount = A.cnt[g];
                 }
-                g = lo;
             }
-            sitem = it;
-            sgeom = g;
         }
         __syncthreads();
         const int it = sitem;
@@ -874,11 +915,25 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
             float4 *dst = reinterpret_cast<float4 *>(sd);
             for (int i = tid; i < nj * DS / 4; i += GS_THREADS) dst[i] = src[i];
             if (tid < 6) reinterpret_cast<float4 *>(&srec)[tid] = reinterpret_cast<const float4 *>(&A.rec[g])[tid];
+            if (tid < A.n_bpg && tid < GS_WROWS) {
+                // C_0 D = 1 - sum u, C_n D = u_n, D = 1 - sum n u_n/(n+2)   (Sec. 2.1.3)
+                const float *u = A.ld + ((size_t)g * A.n_bpg + tid) * A.N;
+                float su = 0.0f, sdn = 0.0f;
+#pragma unroll
+                for (int n = 1; n < NP1; ++n) {
+                    const float un = u[n - 1];
+                    su += un;
+                    sdn += (float)n * un / (float)(n + 2);
+                    swt[tid][n] = un;
+                }
+                swt[tid][0] = 1.0f - su;
+                swt[tid][NP1] = 1.0f - sdn;
+            }
             staged = g;
         }
         __syncthreads();
-        const int i = (it - A.pref[g]) * GS_THREADS + tid;
-        const bool own = i < A.cnt[g];
+        const int i = (it - sfirst) * GS_THREADS + tid;
+        const bool own = i < scount;
         const int t = own ? A.list[(size_t)g * A.n_t + i] : 0;
         float dt = 0.0f;
         if (own) {
@@ -972,18 +1027,30 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
 #pragma unroll 1
             for (int bb = 0; bb < A.n_bpg; ++bb) {
                 size_t row = (size_t)g * A.n_bpg + bb;
-                const float *u = A.ld + row * A.N;
-                // C_0 = (1 - sum u)/D, C_n = u_n/D, D = 1 - sum n u_n/(n+2)   (Sec. 2.1.3)
-                float su = 0.0f, sdn = 0.0f;
-                for (int n = 1; n <= A.N; ++n) {
-                    float un = u[n - 1];
-                    su += un;
-                    sdn += (float)n * un / (float)(n + 2);
-                }
-                float acc_f = (1.0f - su) * al[0];
+                // C_0 = (1 - sum u)/D, C_n = u_n/D, D = 1 - sum n u_n/(n+2)   (Sec. 2.1.3);
+                // the first GS_WROWS passbands' (1 - sum u, u_n, D) were staged
+                // with the geometry, the others are formed here the same way
+                float wt[NP1 + 1];
+                if (bb < GS_WROWS) {
 #pragma unroll
-                for (int n = 1; n < NP1; ++n) acc_f = fmaf(u[n - 1], al[n], acc_f);
-                A.flux[row * A.n_t + t] = 1.0f - acc_f / (1.0f - sdn) * inv_nss;
+                    for (int n = 0; n <= NP1; ++n) wt[n] = swt[bb][n];
+                } else {
+                    const float *u = A.ld + row * A.N;
+                    float su = 0.0f, sdn = 0.0f;
+#pragma unroll
+                    for (int n = 1; n < NP1; ++n) {
+                        const float un = u[n - 1];
+                        su += un;
+                        sdn += (float)n * un / (float)(n + 2);
+                        wt[n] = un;
+                    }
+                    wt[0] = 1.0f - su;
+                    wt[NP1] = 1.0f - sdn;
+                }
+                float acc_f = wt[0] * al[0];
+#pragma unroll
+                for (int n = 1; n < NP1; ++n) acc_f = fmaf(wt[n], al[n], acc_f);
+                A.flux[row * A.n_t + t] = 1.0f - acc_f / wt[NP1] * inv_nss;
             }
         }
     }
@@ -1071,10 +1138,11 @@ __global__ void __launch_bounds__(GS_THREADS) gim_zi_kernel(GimArgs A, const flo
     float *stab = reinterpret_cast<float *>(dsm);   // [nz][N+1]
     float *salpha = stab + nz * NP1;                // [N+1][GS_THREADS]
     __shared__ GeomRec srec;
-    __shared__ int sitem, sgeom, sbad;
+    __shared__ int sitem, sgeom, sfirst, scount, sbad;
 
     const int nss = A.n_ss;
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int total = A.pref[A.n_geom];
     const float inv_nss = 1.0f / (float)nss;
     int nbad = 0;
@@ -1083,20 +1151,20 @@ __global__ void __launch_bounds__(GS_THREADS) gim_zi_kernel(GimArgs A, const flo
 
 #pragma unroll 1
     for (;;) {
-        if (tid == 0) {
-            int it = atomicAdd(A.ctr, 1);
+        if (warp == 0) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(A.ctr, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
             int g = -1;
-            if (it < total) {   // the largest g with pref[g] <= it
-                int lo = 0, hi = A.n_geom - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (A.pref[mid] <= it) lo = mid;
-                    else hi = mid - 1;
+            if (it < total) g = item_geometry(A.pref, A.n_geom, it, lane);
+            if (lane == 0) {
+                sitem = it;
+                sgeom = g;
+                if (g >= 0) {
+                    sfirst = A.pref[g];
+                    scount = A.cnt[g];
                 }
-                g = lo;
             }
-            sitem = it;
-            sgeom = g;
         }
         __syncthreads();
         const int it = sitem;
@@ -1110,8 +1178,8 @@ __global__ void __launch_bounds__(GS_THREADS) gim_zi_kernel(GimArgs A, const flo
         }
         for (int n = 0; n < NP1; ++n) salpha[n * GS_THREADS + tid] = 0.0f;
         __syncthreads();
-        const int i = (it - A.pref[g]) * GS_THREADS + tid;
-        if (i < A.cnt[g]) {
+        const int i = (it - sfirst) * GS_THREADS + tid;
+        if (i < scount) {
             const int t = A.list[(size_t)g * A.n_t + i];
             float2 ts = A.tsplit[t];
             float dt = pt::reduce_time(ts.x, ts.y, srec);
@@ -1191,7 +1259,7 @@ constexpr int MA_SSB = 16;    // supersamples per batch
 __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
 {
     __shared__ GeomRec srec;
-    __shared__ int sitem, sgeom, sbad;
+    __shared__ int sitem, sgeom, sfirst, scount, sbad;
     __shared__ int swarp[MA_PPI / 32];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -1209,20 +1277,20 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
     if (tid == 0) sbad = 0;
 #pragma unroll 1
     for (;;) {
-        if (tid == 0) {
-            int it = atomicAdd(A.ctr, 1);
+        if (warp == 0) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(A.ctr, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
             int g = -1;
-            if (it < total) {   // the largest g with pref[g] <= it
-                int lo = 0, hi = A.n_geom - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (A.pref[mid] <= it) lo = mid;
-                    else hi = mid - 1;
+            if (it < total) g = item_geometry(A.pref, A.n_geom, it, lane);
+            if (lane == 0) {
+                sitem = it;
+                sgeom = g;
+                if (g >= 0) {
+                    sfirst = A.pref[g];
+                    scount = A.cnt[g];
                 }
-                g = lo;
             }
-            sitem = it;
-            sgeom = g;
         }
         __syncthreads();
         const int it = sitem;
@@ -1233,8 +1301,8 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
             staged = g;
         }
         __syncthreads();
-        const int i = (it - A.pref[g]) * MA_PPI + tid;
-        const bool own = i < A.cnt[g];
+        const int i = (it - sfirst) * MA_PPI + tid;
+        const bool own = i < scount;
         const int t = own ? A.list[(size_t)g * A.n_t + i] : 0;
         float dt = 0.0f;
         if (own) {
