@@ -232,7 +232,13 @@ int pt_ma_quad_interp(pt_ma_table table, const double *t_dev, int n_t, const pt_
  * (complete elliptic integrals), then the chain rule through z, Kepler's
  * equation and the conjunction anchor.  e and w may be NULL (circular,
  * w = pi/2); their gradient entries are then d/de and d/dw at e = 0.
- * work_dev: at least pt_ma_quad_bwd_work_bytes(n_t) bytes (time split).
+ * work_dev: at least pt_ma_quad_bwd_work_bytes(n_t) bytes, 16-byte aligned
+ * (else PT_ERR_WORKSPACE): the double-float split of the times, and per tile
+ * of 64 consecutive times (as stored in t_dev; they need not be sorted) the
+ * tile's time range and its residual sum with the flux at 1,
+ * sum wt (y - 1)^2, in FP64.  A tile whose range meets no transit window of
+ * a vector is not evaluated for it: its flux is exactly 1 there and its
+ * derivatives zero, so its residual sum is added as it stands.
  * y_dev, wt_dev: [n_t]; wt may be NULL.  ssr_dev, flux_dev may be NULL.
  * ---------------------------------------------------------------------- */
 typedef struct pt_theta {

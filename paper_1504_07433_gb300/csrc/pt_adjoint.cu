@@ -349,6 +349,8 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
 
 struct BwdArgs {
     const float2 *tsplit;
+    const float2 *tile_mm;    // [n_tiles] smallest and largest time of each tile of TT times
+    const double *tile_ssr;   // [n_tiles] sum of wt (y - 1)^2 over each tile
     int n_t;
     pt_theta th;
     int n_ss;
@@ -359,20 +361,78 @@ struct BwdArgs {
     int *n_bad;
 };
 
-__global__ void tsplit_kernel(const double *t, int n, float2 *out)
+// Per tile of TT times (one CTA of TT threads): the double-float split of
+// each time, the tile's smallest and largest time (rounded outward to FP32)
+// and the residual sum of its times with the flux at 1, sum wt (y - 1)^2, in
+// FP64 and a fixed order.  The adjoint kernel skips tiles that meet no
+// transit window, where the flux is exactly 1 and every derivative zero, and
+// takes their residual sums from here.
+constexpr int TT = 64;   // times per tile
+
+__global__ void __launch_bounds__(TT) tile_kernel(const double *t, const float *y, const float *wt, int n,
+                                                  float2 *tsplit, float2 *tile_mm, double *tile_ssr)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double smin[TT / 32], smax[TT / 32], ssum[TT / 32];
+    const int i = blockIdx.x * TT + threadIdx.x;
+    double lo = INFINITY, hi = -INFINITY, r2 = 0.0;
     if (i < n) {
-        double x = t[i];
-        float h = (float)x;
-        out[i] = make_float2(h, (float)(x - (double)h));
+        const double x = t[i];
+        const float h = (float)x;
+        tsplit[i] = make_float2(h, (float)(x - (double)h));
+        lo = hi = x;
+        const double r = 1.0 - (double)y[i];
+        r2 = (wt ? (double)wt[i] : 1.0) * r * r;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    }
+    if (lane == 0) {
+        smin[warp] = lo;
+        smax[warp] = hi;
+        ssum[warp] = r2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < TT / 32; ++w) {
+            lo = fmin(lo, smin[w]);
+            hi = fmax(hi, smax[w]);
+            r2 += ssum[w];
+        }
+        float flo = (float)lo, fhi = (float)hi;
+        if ((double)flo > lo) flo = nextafterf(flo, -INFINITY);
+        if ((double)fhi < hi) fhi = nextafterf(fhi, INFINITY);
+        tile_mm[blockIdx.x] = make_float2(flo, fhi);
+        tile_ssr[blockIdx.x] = r2;
     }
 }
+
+// Can a time in [tmin, tmax] lie in the transit window of some epoch,
+// t - t0 - n P in [win_lo, win_hi]?  That is, is there an integer n with
+// (tmin - t0 - win_hi) / P <= n <= (tmax - t0 - win_lo) / P?  The interval
+// is widened by m, 1e-6 of the magnitudes involved, which exceeds the FP32
+// rounding of these expressions, so the test never misses an epoch.
+__device__ __forceinline__ bool tile_meets_window(const pt::GeomRec &g, float tmin, float tmax)
+{
+    if (g.win_lo > g.win_hi) return false;                // never in transit
+    if (g.win_hi - g.win_lo >= 0.5f * g.Ph) return true;  // a wide window: no test
+    const float m = 1e-6f * (fabsf(tmin) + fabsf(tmax) + fabsf(g.t0h) + g.Ph) + 1e-9f;
+    const float n_lo = ceilf((tmin - g.t0h - g.win_hi - m) * g.invP);
+    const float n_hi = floorf((tmax - g.t0h - g.win_lo + m) * g.invP);
+    return n_lo <= n_hi;
+}
+
 
 __global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
 {
     __shared__ VecConst sc;
     __shared__ float sred[TB / 32][10];
+    __shared__ double sout[TB / 32];
+    __shared__ int slist[TB];          // the current chunk's evaluated tiles, in order
+    __shared__ int swcnt[TB / 32];
     __shared__ int sbad;
     const int v = blockIdx.x;
     if (threadIdx.x == 0) {
@@ -386,18 +446,71 @@ __global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
     for (int i = 0; i < 10; ++i) acc[i] = 0.0f;
     bool bad = false;
     const float inv_ss = 1.0f / (float)A.n_ss;
-    // the next time's inputs are loaded one iteration ahead
-    float2 ts_n = threadIdx.x < A.n_t ? A.tsplit[threadIdx.x] : make_float2(0.0f, 0.0f);
-    float y_n = threadIdx.x < A.n_t ? A.y[threadIdx.x] : 0.0f;
-    float w_n = (A.wt && threadIdx.x < A.n_t) ? A.wt[threadIdx.x] : 1.0f;
-    for (int i = threadIdx.x; i < A.n_t; i += TB) {
+    const int n_tiles = (A.n_t + TT - 1) / TT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double ssr_out = 0.0;   // this thread's share of the skipped tiles' residual sums
+    // Tile j holds times j TT .. j TT + TT - 1.  A tile that meets no transit
+    // window has flux 1 and zero derivatives: it is skipped and its residual
+    // sum comes from tile_kernel.  Chunks of TB tiles: one window test per
+    // thread, the evaluated tiles listed in order in shared memory, then
+    // passes over TB / TT of them at a time (thread tid takes time tid % TT of
+    // list entry tid / TT), each pass's inputs loaded during the previous one.
+    constexpr int TPP = TB / TT;   // tiles per pass
+    for (int c0 = 0; c0 < n_tiles; c0 += TB) {
+        const int jt = c0 + (int)threadIdx.x;
+        bool ev = false;
+        if (jt < n_tiles) {
+            const float2 mm = A.tile_mm[jt];
+            ev = tile_meets_window(c.g, mm.x, mm.y);
+            if (!ev) ssr_out += A.tile_ssr[jt];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ev);
+        __syncthreads();   // the previous chunk's list is no longer read
+        if (lane == 0) swcnt[warp] = __popc(bal);
+        __syncthreads();
+        int base = 0, n_ev = 0;
+#pragma unroll
+        for (int w = 0; w < TB / 32; ++w) {
+            base += (w < warp) ? swcnt[w] : 0;
+            n_ev += swcnt[w];
+        }
+        if (ev) slist[base + __popc(bal & ((1u << lane) - 1u))] = jt;
+        if (A.flux) {
+            // flux 1 on this chunk's skipped tiles: thread tid writes time
+            // tid % TT of every (TB / TT)-th tile
+            const int c1 = min(n_tiles, c0 + TB);
+            for (int tj = c0 + (int)(threadIdx.x / TT); tj < c1; tj += TPP) {
+                const int i = tj * TT + (int)(threadIdx.x % TT);
+                const float2 mm = A.tile_mm[tj];
+                if (i < A.n_t && !tile_meets_window(c.g, mm.x, mm.y)) A.flux[(size_t)v * A.n_t + i] = 1.0f;
+            }
+        }
+        __syncthreads();
+        // pass q takes list entries q TPP .. q TPP + TPP - 1
+        auto time_of = [&](int q) {
+            const int e = q * TPP + (int)(threadIdx.x / TT);
+            return e < n_ev ? slist[e] * TT + (int)(threadIdx.x % TT) : -1;
+        };
+        const int n_pass = (n_ev + TPP - 1) / TPP;
+        int i_n = n_pass > 0 ? time_of(0) : -1;
+        float2 ts_n = make_float2(0.0f, 0.0f);
+        float y_n = 0.0f, w_n = 1.0f;
+        if (i_n >= 0 && i_n < A.n_t) {
+            ts_n = A.tsplit[i_n];
+            y_n = A.y[i_n];
+            w_n = A.wt ? A.wt[i_n] : 1.0f;
+        }
+        for (int q = 0; q < n_pass; ++q) {
+        const int i = i_n;
         const float2 ts = ts_n;
         const float yi = y_n, wi = w_n;
-        if (i + TB < A.n_t) {
-            ts_n = A.tsplit[i + TB];
-            y_n = A.y[i + TB];
-            w_n = A.wt ? A.wt[i + TB] : 1.0f;
+        i_n = q + 1 < n_pass ? time_of(q + 1) : -1;
+        if (i_n >= 0 && i_n < A.n_t) {
+            ts_n = A.tsplit[i_n];
+            y_n = A.y[i_n];
+            w_n = A.wt ? A.wt[i_n] : 1.0f;
         }
+        if (i < 0 || i >= A.n_t) continue;
         // epoch and offset (double-float phase reduction)
         float s = ts.x - c.g.t0h;
         float n_ep = rintf(s * c.g.invP);
@@ -430,10 +543,13 @@ __global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
         float tw = 2.0f * wi * res;
 #pragma unroll
         for (int j = 0; j < 9; ++j) acc[j] = fmaf(tw, gp[j], acc[j]);
+        }
     }
     if (bad) atomicAdd(&sbad, 1);
-    // deterministic block reduction
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // deterministic block reduction (the skipped tiles' sums in FP64)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ssr_out += __shfl_xor_sync(0xffffffffu, ssr_out, o);
+    if (lane == 0) sout[warp] = ssr_out;
 #pragma unroll
     for (int j = 0; j < 10; ++j) {
         float x = acc[j];
@@ -442,13 +558,17 @@ __global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
         if (lane == 0) sred[warp][j] = x;
     }
     __syncthreads();
+    __syncthreads();
     if (threadIdx.x < 10) {
         float x = 0.0f;
         for (int w = 0; w < TB / 32; ++w) x += sred[w][threadIdx.x];
-        if (threadIdx.x < 9)
+        if (threadIdx.x < 9) {
             A.grad[(size_t)v * 9 + threadIdx.x] = x;
-        else if (A.ssr)
-            A.ssr[v] = x;
+        } else if (A.ssr) {
+            double so = 0.0;
+            for (int w = 0; w < TB / 32; ++w) so += sout[w];
+            A.ssr[v] = (float)((double)x + so);
+        }
     }
     if (threadIdx.x == 0 && sbad && A.n_bad) atomicAdd(A.n_bad, sbad);
 }
@@ -457,7 +577,17 @@ __global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
 
 extern "C" {
 
-size_t pt_ma_quad_bwd_work_bytes(int n_t) { return n_t > 0 ? ((size_t)n_t * sizeof(float2) + 255) & ~(size_t)255 : 256; }
+// work buffer: [n_t] time split, then per tile of TT times its time range
+// and its residual sum with the flux at 1, each part 256-byte aligned
+static size_t bwd_split_bytes(int n_t) { return ((size_t)n_t * sizeof(float2) + 255) & ~(size_t)255; }
+static size_t bwd_tiles(int n_t) { return ((size_t)n_t + TT - 1) / TT; }
+
+size_t pt_ma_quad_bwd_work_bytes(int n_t)
+{
+    if (n_t <= 0) return 256;
+    const size_t nt = bwd_tiles(n_t);
+    return bwd_split_bytes(n_t) + ((nt * sizeof(float2) + 255) & ~(size_t)255) + ((nt * sizeof(double) + 255) & ~(size_t)255);
+}
 
 int pt_ma_quad_bwd(const double *t, int n_t, const pt_theta *th, int n_ss, double t_exp, int max_iter,
                    const float *y, const float *wt, float *grad, float *ssr, float *flux, void *work,
@@ -474,13 +604,20 @@ int pt_ma_quad_bwd(const double *t, int n_t, const pt_theta *th, int n_ss, doubl
     if (!work) return PT_ERR_WORKSPACE;
     if (work_bytes < pt_ma_quad_bwd_work_bytes(n_t)) return PT_ERR_WORKSPACE;
     if (th->n_v > 0x7fffffff) return PT_ERR_ARG;
+    if (((uintptr_t)work & 15u) != 0u)
+        return pt_internal::set_error(PT_ERR_WORKSPACE, "pt_ma_quad_bwd", "work buffer must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
+    const size_t nt = bwd_tiles(n_t);
     float2 *ts = (float2 *)work;
-    tsplit_kernel<<<(n_t + 255) / 256, 256, 0, s>>>(t, n_t, ts);
+    float2 *tmm = (float2 *)((char *)work + bwd_split_bytes(n_t));
+    double *tssr = (double *)((char *)tmm + ((nt * sizeof(float2) + 255) & ~(size_t)255));
+    tile_kernel<<<(unsigned)nt, TT, 0, s>>>(t, y, wt, n_t, ts, tmm, tssr);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return pt_internal::set_error(PT_ERR_CUDA, "tsplit_kernel", cudaGetErrorString(e));
+    if (e != cudaSuccess) return pt_internal::set_error(PT_ERR_CUDA, "tile_kernel", cudaGetErrorString(e));
     BwdArgs A;
     A.tsplit = ts;
+    A.tile_mm = tmm;
+    A.tile_ssr = tssr;
     A.n_t = n_t;
     A.th = *th;
     A.n_ss = n_ss;

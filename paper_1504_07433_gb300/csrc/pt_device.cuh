@@ -204,36 +204,59 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
 // a K + (b - a) ... is folded into (a, b) by the caller), the second has
 // p = rho > 0 and b = 0.  Converged when the arithmetic-geometric means agree
 // to 3e-4 (quadratic convergence then leaves ~1e-7); at most 10 steps.
+// The two integrals' updates run as the two lanes of fma/mul/add.rn.f32x2
+// (one instruction for both; each lane rounded as the scalar operation).
 // ---------------------------------------------------------------------------
+// two-lane FP32 helpers (sm_100 and later); each lane is one IEEE operation
+// rounded once, the same result as the scalar instruction
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
+{
+    return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float f2_lo(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f2_hi(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __device__ __forceinline__ void cel2(float kc, float a1, float b1, float rho, float a2, float *r1,
                                      float *r2)
 {
-    float p1 = 1.0f;
-    float p2 = fast_sqrt(rho);
-    float b2 = 0.0f;
+    // lanes: (first integral, second integral)
+    unsigned long long A = f2_pack(a1, a2), B = f2_pack(b1, 0.0f), P = f2_pack(1.0f, fast_sqrt(rho));
     float m = 1.0f, e = kc;
 #pragma unroll 1
     for (int it = 0; it < 10; ++it) {
-        float ip1 = __fdividef(1.0f, p1);
-        float ip2 = __fdividef(1.0f, p2);
-        float f = a1;
-        a1 = fmaf(b1, ip1, a1);
-        float g = e * ip1;
-        b1 = 2.0f * fmaf(f, g, b1);
-        p1 += g;
-        f = a2;
-        a2 = fmaf(b2, ip2, a2);
-        g = e * ip2;
-        b2 = 2.0f * fmaf(f, g, b2);
-        p2 += g;
-        g = m;
+        const unsigned long long ip = f2_pack(__fdividef(1.0f, f2_lo(P)), __fdividef(1.0f, f2_hi(P)));
+        const unsigned long long F = A;
+        A = f2_fma(B, ip, A);
+        const unsigned long long G = f2_mul(f2_pack(e, e), ip);
+        B = f2_fma(F, G, B);
+        B = f2_add(B, B);
+        P = f2_add(P, G);
+        float g = m;
         m = kc + m;
         if (fabsf(g - kc) <= g * 3e-4f) break;
         kc = 2.0f * fast_sqrt(e);
         e = kc * m;
     }
-    *r1 = __fdividef((0.5f * PT_PI_F) * fmaf(a1, m, b1), m * (m + p1));
-    *r2 = __fdividef((0.5f * PT_PI_F) * fmaf(a2, m, b2), m * (m + p2));
+    *r1 = __fdividef((0.5f * PT_PI_F) * fmaf(f2_lo(A), m, f2_lo(B)), m * (m + f2_lo(P)));
+    *r2 = __fdividef((0.5f * PT_PI_F) * fmaf(f2_hi(A), m, f2_hi(B)), m * (m + f2_hi(P)));
 }
 
 // cel2's loop carrying K = cel(kc, 1, 1, 1) and E = cel(kc, 1, 1, kc^2) in place

@@ -137,3 +137,41 @@ def test_adjoint_full_size_sampled(torch_cuda):
     tol = _bound(wl["t"], rows, y.astype(np.float64), None, 1, 0.0)
     assert np.all(np.abs(g[idx] - grad_r) <= tol)
     assert np.allclose(ssr.cpu().numpy()[idx], ssr_r, rtol=2e-4)
+
+
+def test_adjoint_tile_skipping_epochs_and_order(torch_cuda):
+    """Tiles of 64 times that meet no transit window are skipped (flux 1,
+    residual sum from the tile's FP64 sum of wt (y - 1)^2).  Times over ten
+    orbits, and the same times shuffled so that every tile spans them all (no
+    tile can be skipped): flux bitwise the same point by point, residual sums
+    and gradients of both orders against the oracle."""
+    torch = torch_cuda
+    import paper_1504_07433_gb300 as pt
+    n_v, n_t = 6, 3000
+    wl = W.adjoint(n_v=n_v, n_t=n_t)
+    rng = np.random.default_rng(21)
+    t_sorted = np.sort(rng.uniform(-10.0, 20.0, n_t))
+    perm = rng.permutation(n_t)
+    true = wl["true"]
+    th_true = np.array([true[nm] for nm in ("t0", "P", "a", "b", "e", "w", "k", "u1", "u2")])
+    y = np.array([oracle.flux_theta(tj, th_true, 1, 0.0) for tj in t_sorted])
+    y = (y + rng.normal(0, 1e-4, n_t)).astype(np.float32)
+    wt = rng.uniform(0.5, 2.0, n_t).astype(np.float32)
+    th = pt.theta_to_device(wl["theta"])
+    rows = _theta_rows(wl["theta"], slice(0, n_v))
+    out = {}
+    for name, order in (("sorted", np.arange(n_t)), ("shuffled", perm)):
+        t = torch.as_tensor(t_sorted[order], dtype=torch.float64, device="cuda")
+        ssr, grad, flux = pt.ma_quad_bwd(t, th, torch.as_tensor(y[order], device="cuda"),
+                                         torch.as_tensor(wt[order], device="cuda"), want_flux=True)
+        f = np.empty((n_v, n_t), np.float32)
+        f[:, order] = flux.cpu().numpy()
+        out[name] = (ssr.cpu().numpy().astype(np.float64), grad.cpu().numpy().astype(np.float64), f)
+    assert np.array_equal(out["sorted"][2], out["shuffled"][2])
+    assert (out["sorted"][2] < 1).sum() > 0
+    ssr_r, grad_r = oracle.ssr_grad(t_sorted, rows, y.astype(np.float64), wt.astype(np.float64))
+    tol = _bound(t_sorted, rows, y.astype(np.float64), wt.astype(np.float64), 1, 0.0)
+    for name in out:
+        s, g, _ = out[name]
+        assert np.allclose(s, ssr_r, rtol=2e-4, atol=1e-9), name
+        assert np.all(np.abs(g - grad_r) <= tol), name
