@@ -365,7 +365,8 @@ struct GimArgs {
     int max_iter;
     float *flux;          // [rows][n_t]
     int *cnt;             // [n_geom] listed pairs per geometry
-    int *pref;            // [n_geom + 1] work items before each geometry
+    int *pref;            // [n_geom + 1] work items before each position of the geometry order
+    int *gord;            // [n_geom] geometry at each position of the order
     int *ctr;             // next work item of the evaluation kernel
     int *list;            // [n_geom][n_t] time indices of listed pairs
     int ppi;              // pairs per work item (GS_THREADS or MA_PPI)
@@ -583,20 +584,92 @@ __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A, TableJob J, i
 
 // pref[g] = sum over g' < g of ceil(cnt[g'] / ppi); pref[n_geom] = total.
 // One CTA of 1024 threads; also rewinds the evaluation kernels' item counter.
-__global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_geom, int ppi, int *pref, int *ctr)
+// Work items in a cost order: geometries sorted by an estimate of the
+// in-transit supersamples per listed pair, largest first, so that the items
+// handed out last are the cheap ones and the persistent CTAs finish close
+// together.  The window of a geometry is its transit plus half an exposure on
+// each side (and margins), so a listed pair is in transit for about a
+// fraction (W - t_exp) / W of its exposure, W = win_hi - win_lo.  Ties (and
+// every geometry when there is no exposure time) keep their index order.
+// gord[p] is the geometry at position p; pref[p] the items before position p.
+// Up to 1,024 geometries each thread counts the geometries before its own
+// (no barriers), up to SCAN_SORT_MAX a bitonic sort in shared memory, above
+// that the order is the index order.  The Mandel-Agol pairs kernel (order =
+// false: items of a few microseconds, and measured slower with the cost
+// order) takes the index order.
+constexpr int SCAN_SORT_MAX = 4096;
+
+__device__ __forceinline__ float scan_key(const int *cnt, const GeomRec *rec, float t_exp, int g)
+{
+    const float w = rec[g].win_hi - rec[g].win_lo;
+    return (cnt[g] > 0 && w > 0.0f) ? fmaxf(w - t_exp, 0.0f) / w : -1.0f;
+}
+
+__global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, const GeomRec *rec, float t_exp, int n_geom,
+                                                        int ppi, bool order, int *pref, int *gord, int *ctr)
 {
     __shared__ int swarp[32];
     __shared__ int scarry;
+    __shared__ float skey[SCAN_SORT_MAX];
+    __shared__ int sidx[SCAN_SORT_MAX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = blockDim.x >> 5;
+    const bool sorted = order && n_geom <= SCAN_SORT_MAX;
     if (threadIdx.x == 0) {
         scarry = 0;
         *ctr = 0;
     }
+    if (sorted && n_geom <= (int)blockDim.x) {
+        // one thread per geometry: its position is the number of geometries
+        // before it in the order
+        const int i = threadIdx.x;
+        if (i < n_geom) skey[i] = scan_key(cnt, rec, t_exp, i);
+        __syncthreads();
+        if (i < n_geom) {
+            const float ki = skey[i];
+            int r = 0;
+            for (int j = 0; j < n_geom; ++j) {
+                const float kj = skey[j];
+                r += (kj > ki || (kj == ki && j < i)) ? 1 : 0;
+            }
+            sidx[r] = i;
+        }
+        __syncthreads();
+    } else if (sorted) {
+        int n2 = 1;
+        while (n2 < n_geom) n2 <<= 1;
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+            skey[i] = i < n_geom ? scan_key(cnt, rec, t_exp, i) : -2.0f;   // padding sorts last
+            sidx[i] = i;
+        }
+        __syncthreads();
+        // bitonic sort: key descending, index ascending among equal keys
+        for (int kk = 2; kk <= n2; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const float ki = skey[i], kl = skey[l];
+                        const int ii = sidx[i], il = sidx[l];
+                        const bool i_first = ki > kl || (ki == kl && ii < il);
+                        const bool up = (i & kk) == 0;   // this block in the final order
+                        if (up != i_first) {
+                            skey[i] = kl;
+                            skey[l] = ki;
+                            sidx[i] = il;
+                            sidx[l] = ii;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int p = threadIdx.x; p < n_geom; p += blockDim.x) gord[p] = sorted ? sidx[p] : p;
     __syncthreads();
     for (int base = 0; base < n_geom; base += blockDim.x) {
-        int g = base + threadIdx.x;
-        int v = (g < n_geom) ? (cnt[g] + ppi - 1) / ppi : 0;
+        int p = base + threadIdx.x;
+        int v = (p < n_geom) ? (cnt[sorted ? sidx[p] : p] + ppi - 1) / ppi : 0;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -616,7 +689,7 @@ __global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, int n_ge
         }
         __syncthreads();
         int incl = scarry + (warp > 0 ? swarp[warp - 1] : 0) + x;
-        if (g < n_geom) pref[g] = incl - v;
+        if (p < n_geom) pref[p] = incl - v;
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) scarry = incl;
         __syncthreads();
@@ -866,7 +939,7 @@ __device__ __forceinline__ void cheb_round(const float *sd, int nj, const float2
 }
 
 template <int NP1>
-__global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const float *dtab)
+__global__ void __launch_bounds__(GS_THREADS, 5) gim_cheb_kernel(GimArgs A, const float *dtab)
 {
     constexpr int DS = (NP1 + 3) & ~3;        // floats per coefficient row
     constexpr int CH = GS_GMAX * GS_THREADS;  // entries of the largest round
@@ -895,16 +968,16 @@ __global__ void __launch_bounds__(GS_THREADS) gim_cheb_kernel(GimArgs A, const f
             int it = 0;
             if (lane == 0) it = atomicAdd(A.ctr, 1);
             it = __shfl_sync(0xffffffffu, it, 0);
-            int g = -1;
-            if (it < total) g = item_geometry(A.pref, A.n_geom, it, lane);
-            if (lane == 0) {
-                sitem = it;
-                sgeom = g;
-                if (g >= 0) {
-                    sfirst = A.pref[g];
+            if (it < total) {
+                const int pos = item_geometry(A.pref, A.n_geom, it, lane);
+                if (lane == 0) {
+                    const int g = A.gord[pos];
+                    sgeom = g;
+                    sfirst = A.pref[pos];
                     scount = A.cnt[g];
                 }
             }
+            if (lane == 0) sitem = it;
         }
         __syncthreads();
         const int it = sitem;
@@ -1155,16 +1228,16 @@ __global__ void __launch_bounds__(GS_THREADS) gim_zi_kernel(GimArgs A, const flo
             int it = 0;
             if (lane == 0) it = atomicAdd(A.ctr, 1);
             it = __shfl_sync(0xffffffffu, it, 0);
-            int g = -1;
-            if (it < total) g = item_geometry(A.pref, A.n_geom, it, lane);
-            if (lane == 0) {
-                sitem = it;
-                sgeom = g;
-                if (g >= 0) {
-                    sfirst = A.pref[g];
+            if (it < total) {
+                const int pos = item_geometry(A.pref, A.n_geom, it, lane);
+                if (lane == 0) {
+                    const int g = A.gord[pos];
+                    sgeom = g;
+                    sfirst = A.pref[pos];
                     scount = A.cnt[g];
                 }
             }
+            if (lane == 0) sitem = it;
         }
         __syncthreads();
         const int it = sitem;
@@ -1281,16 +1354,16 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
             int it = 0;
             if (lane == 0) it = atomicAdd(A.ctr, 1);
             it = __shfl_sync(0xffffffffu, it, 0);
-            int g = -1;
-            if (it < total) g = item_geometry(A.pref, A.n_geom, it, lane);
-            if (lane == 0) {
-                sitem = it;
-                sgeom = g;
-                if (g >= 0) {
-                    sfirst = A.pref[g];
+            if (it < total) {
+                const int pos = item_geometry(A.pref, A.n_geom, it, lane);
+                if (lane == 0) {
+                    const int g = A.gord[pos];
+                    sgeom = g;
+                    sfirst = A.pref[pos];
                     scount = A.cnt[g];
                 }
             }
+            if (lane == 0) sitem = it;
         }
         __syncthreads();
         const int it = sitem;
@@ -1662,8 +1735,8 @@ WorkLayout work_layout(int n_t, int n_v, int n_b, int k_per_band, int NP1, int n
         off += align256((size_t)n_geom * NP1 * n_j * sizeof(float4));
         L.cnt = off;
         off += align256((size_t)(n_geom + 1) * sizeof(int));
-        L.pref = off;
-        off += align256((size_t)(n_geom + 1) * sizeof(int));
+        L.pref = off;   // the item prefix [n_geom + 1], then the geometry order [n_geom]
+        off += align256((size_t)(2 * n_geom + 1) * sizeof(int));
         L.list = off;
         off += align256((size_t)n_geom * n_t * sizeof(int));
         L.fscr = off;
@@ -2064,6 +2137,7 @@ static int ma_quad_list(const double *t, int n_t, const pt_orbit *orb, const flo
     A.flux = flux ? flux : (float *)(wb + L.fscr);
     A.cnt = cnt;
     A.pref = (int *)(wb + L.pref);
+    A.gord = A.pref + n_geom + 1;
     A.ctr = cnt + n_geom;
     A.list = (int *)(wb + L.list);
     A.ppi = MA_PPI;
@@ -2075,7 +2149,7 @@ static int ma_quad_list(const double *t, int n_t, const pt_orbit *orb, const flo
     gim_window_kernel<<<(unsigned)n_cta, TT, 0, s>>>(A, J, n_tiles);
     st = check_launch("gim_window_kernel");
     if (st) return st;
-    gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, MA_PPI, A.pref, A.ctr);
+    gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, A.rec, A.t_exp, n_geom, MA_PPI, false, A.pref, A.gord, A.ctr);
     st = check_launch("gim_scan_kernel");
     if (st) return st;
     const size_t msm = ma_pairs_smem(n_ss);   // at most 44 KB: no opt-in needed
@@ -2371,6 +2445,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     A.flux = flux ? flux : (float *)(wb + L.fscr);
     A.cnt = cnt;
     A.pref = (int *)(wb + L.pref);
+    A.gord = A.pref + n_geom + 1;
     A.ctr = cnt + n_geom;
     A.list = (int *)(wb + L.list);
     A.ppi = GS_THREADS;   // work items of GS_THREADS listed pairs
@@ -2406,7 +2481,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
         if (st) return st;
     }
     float *dtab = (float *)(wb + L.dtab);
-    gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, n_geom, A.ppi, A.pref, A.ctr);
+    gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, A.rec, A.t_exp, n_geom, A.ppi, true, A.pref, A.gord, A.ctr);
     st = check_launch("gim_scan_kernel");
     if (st) return st;
     const size_t max_items = (size_t)n_geom * ((n_t + GS_THREADS - 1) / GS_THREADS);
