@@ -298,7 +298,12 @@ typedef struct pt_batch_desc {
     int k_mode;             /* 0: each passband with its own k (exact);
                                1: the model once per walker with k_hat, the mean of its
                                   passbands' k, and each passband's depth 1 - f scaled by
-                                  k_b^2 / k_hat^2 (Sec. 3.5) */
+                                  k_b^2 / k_hat^2 (Sec. 3.5);
+                               2: each passband with its own k, the Mandel-Agol terms read
+                                  from `table` by bilinear interpolation in (k, z)
+                                  (Sec. 2.2.3; k outside the table's range is clamped) */
+    pt_ma_table table;      /* k_mode 2: a table of pt_ma_table_create, owned by the caller
+                               and kept alive while the plan runs; NULL otherwise */
 } pt_batch_desc;
 
 typedef struct pt_batch_plan_s *pt_batch_plan;

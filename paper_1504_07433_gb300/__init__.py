@@ -520,7 +520,8 @@ class BatchDesc(ctypes.Structure):
     _fields_ = [("t", _c_void_p), ("n_t", _c_int), ("lc_offsets", ctypes.POINTER(_c_int)), ("n_lc", _c_int),
                 ("orb", Orbit), ("k", _c_void_p), ("ld", _c_void_p), ("n_b", _c_int), ("n_ss", _c_int),
                 ("t_exp", _c_double), ("max_iter", _c_int), ("y", _c_void_p), ("wt", _c_void_p),
-                ("flux", _c_void_p), ("ssr", _c_void_p), ("n_bad", _c_void_p), ("k_mode", _c_int)]
+                ("flux", _c_void_p), ("ssr", _c_void_p), ("n_bad", _c_void_p), ("k_mode", _c_int),
+                ("table", _c_void_p)]
 
 
 class BatchPlan:
@@ -532,11 +533,13 @@ class BatchPlan:
     k [n_v, n_b], ld [n_v, n_b, 2], y/wt [n_b, n_t]; flux/ssr are outputs
     ([n_v, n_b, n_t] / [n_v, n_b]); pass want_flux / want_ssr to allocate them.
     k_mode 1 evaluates the model once per walker with the mean k of its
-    passbands and scales each passband's depth by k_b^2 / k_hat^2 (Sec. 3.5).
+    passbands and scales each passband's depth by k_b^2 / k_hat^2 (Sec. 3.5);
+    k_mode 2 reads the Mandel-Agol terms from ``table`` (an MATable, kept
+    alive by the plan) by bilinear interpolation (Sec. 2.2.3).
     """
 
     def __init__(self, t, lc_offsets, orb, k, ld, n_ss=1, t_exp=0.0, max_iter=16, y=None, wt=None,
-                 want_flux=True, want_ssr=False, autotune=True, n_bad=None, k_mode=0):
+                 want_flux=True, want_ssr=False, autotune=True, n_bad=None, k_mode=0, table=None):
         torch = _torch()
         lib = load_library()
         for name, res, args in [("pt_batch_plan_create", _c_int, [ctypes.POINTER(BatchDesc), _c_int,
@@ -556,9 +559,10 @@ class BatchPlan:
         self.ssr = torch.empty((n_v, n_b), dtype=torch.float32, device=t.device) if want_ssr else None
         offs = [int(x) for x in lc_offsets]
         self._offs = (_c_int * len(offs))(*offs)
-        self._keep = (t, orb, k, ld, y, wt, n_bad)
+        self._keep = (t, orb, k, ld, y, wt, n_bad, table)
         d = BatchDesc(_ptr(t), n_t, self._offs, len(offs) - 1, o, _ptr(k), _ptr(ld), n_b, int(n_ss), float(t_exp),
-                      int(max_iter), _ptr(y), _ptr(wt), _ptr(self.flux), _ptr(self.ssr), _ptr(n_bad), int(k_mode))
+                      int(max_iter), _ptr(y), _ptr(wt), _ptr(self.flux), _ptr(self.ssr), _ptr(n_bad), int(k_mode),
+                      table.handle.value if table is not None else None)
         h = _c_void_p()
         _check(lib.pt_batch_plan_create(ctypes.byref(d), int(bool(autotune)), ctypes.byref(h)),
                "pt_batch_plan_create")

@@ -32,6 +32,8 @@ using pt::GeomRec;
 
 namespace pt_internal {
 int set_error(int status, const char *where, const char *msg);   // pt_lc.cu
+bool ma_table_view(pt_ma_table t, const float4 **tab, int *n_k, int *n_z, float *k_lo, float *k_hi, float *inv_dk,
+                   float *inv_dz);                                   // pt_lc.cu
 }
 
 namespace {
@@ -58,6 +60,10 @@ struct BatchArgs {
     int *counter;
     int *n_bad;
     int khat;            // k_mode 1: terms once per time with k_hat (Sec. 3.5)
+    // k_mode 2: the Mandel-Agol terms interpolated from this table (Sec. 2.2.3)
+    const float4 *mtab;
+    int mn_k, mn_z;
+    float mk_lo, mk_hi, minv_dk, minv_dz;
 };
 
 struct BatchSetupArgs {
@@ -100,7 +106,7 @@ __global__ void batch_setup_kernel(BatchSetupArgs s)
     }
 }
 
-template <int TT>
+template <int TT, bool INTERP>
 __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
 {
     extern __shared__ __align__(16) float dyn[];
@@ -209,7 +215,10 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
             float kb = swt[4 * b + 3];
             float le, ld, ed;
             if (A.n_ss == 1) {
-                pt::ma_terms(kb, sz[tl], &le, &ld, &ed);
+                if (INTERP)
+                    pt::ma_interp(A.mtab, A.mn_k, A.mn_z, A.mk_lo, A.mk_hi, A.minv_dk, A.minv_dz, kb, sz[tl], &le, &ld, &ed);
+                else
+                    pt::ma_terms(kb, sz[tl], &le, &ld, &ed);
             } else {
                 le = ld = ed = 0.0f;
                 float warm[3] = {__int_as_float(0x7fffffff), 0.0f, 0.0f};   // Kepler warm start (none yet)
@@ -217,7 +226,10 @@ __global__ void __launch_bounds__(TT) batch_kernel(BatchArgs A)
                     float dts = sdt[tl] + A.t_exp * (((float)s + 0.5f) * inv_ss - 0.5f);
                     float zs = pt::orbit_z<true>(srec, dts, A.max_iter, &bad, warm);
                     float a0, a1, a2;
-                    pt::ma_terms(kb, zs, &a0, &a1, &a2);
+                    if (INTERP)
+                        pt::ma_interp(A.mtab, A.mn_k, A.mn_z, A.mk_lo, A.mk_hi, A.minv_dk, A.minv_dz, kb, zs, &a0, &a1, &a2);
+                    else
+                        pt::ma_terms(kb, zs, &a0, &a1, &a2);
                     le += a0;
                     ld += a1;
                     ed += a2;
@@ -310,27 +322,43 @@ void build_items(const pt_batch_plan_s &p, int tt, std::vector<BatchItem> *items
 template <int TT>
 int launch_batch_tt(const BatchArgs &A, int grid, size_t smem, cudaStream_t s)
 {
-    batch_kernel<TT><<<grid, TT, smem, s>>>(A);
+    if (A.mtab)
+        batch_kernel<TT, true><<<grid, TT, smem, s>>>(A);
+    else
+        batch_kernel<TT, false><<<grid, TT, smem, s>>>(A);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PT_OK : berr(e, "batch_kernel");
 }
 
-int set_smem_attr(int tt, size_t smem)
+template <bool I>
+cudaError_t set_smem_attr_i(int tt, size_t smem)
 {
     cudaError_t e = cudaSuccess;
-    if (tt == 64) e = cudaFuncSetAttribute(batch_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (tt == 128) e = cudaFuncSetAttribute(batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (tt == 256) e = cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (tt == 64) e = cudaFuncSetAttribute(batch_kernel<64, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (tt == 128) e = cudaFuncSetAttribute(batch_kernel<128, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (tt == 256) e = cudaFuncSetAttribute(batch_kernel<256, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+int set_smem_attr(int tt, size_t smem, bool interp)
+{
+    cudaError_t e = interp ? set_smem_attr_i<true>(tt, smem) : set_smem_attr_i<false>(tt, smem);
     return e == cudaSuccess ? PT_OK : berr(e, "cudaFuncSetAttribute");
 }
 
-int max_ctas_per_sm(int tt, size_t smem)
+template <bool I>
+int max_ctas_per_sm_i(int tt, size_t smem)
 {
     int n = 0;
-    if (tt == 64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<64>, tt, smem);
-    if (tt == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<128>, tt, smem);
-    if (tt == 256) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<256>, tt, smem);
+    if (tt == 64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<64, I>, tt, smem);
+    if (tt == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<128, I>, tt, smem);
+    if (tt == 256) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<256, I>, tt, smem);
     return n;
+}
+
+int max_ctas_per_sm(int tt, size_t smem, bool interp)
+{
+    return interp ? max_ctas_per_sm_i<true>(tt, smem) : max_ctas_per_sm_i<false>(tt, smem);
 }
 
 // Enqueue one full evaluation (counter reset, set-up, persistent kernel,
@@ -346,7 +374,7 @@ int enqueue(pt_batch_plan_s &p, cudaStream_t s)
     sa.tsplit = p.d_tsplit;
     sa.orb = d.orb;
     sa.k = d.k;
-    sa.khat = d.k_mode;
+    sa.khat = d.k_mode == 1;
     sa.n_b = d.n_b;
     sa.half_exp = (float)(0.5 * d.t_exp);
     sa.rec = p.d_rec;
@@ -359,7 +387,13 @@ int enqueue(pt_batch_plan_s &p, cudaStream_t s)
     A.n_t = d.n_t;
     A.rec = p.d_rec;
     A.k = d.k;
-    A.khat = d.k_mode;
+    A.khat = d.k_mode == 1;
+    A.mtab = nullptr;
+    A.mn_k = A.mn_z = 0;
+    A.mk_lo = A.mk_hi = A.minv_dk = A.minv_dz = 0.0f;
+    if (d.k_mode == 2 && !pt_internal::ma_table_view(d.table, &A.mtab, &A.mn_k, &A.mn_z, &A.mk_lo, &A.mk_hi,
+                                                     &A.minv_dk, &A.minv_dz))
+        return pt_internal::set_error(PT_ERR_ARG, "pt_batch_run", "k_mode 2 needs an interpolation table");
     A.ld = d.ld;
     A.n_v = d.orb.n_v;
     A.n_b = d.n_b;
@@ -412,7 +446,7 @@ int configure(pt_batch_plan_s &p, int tt, int cps)
     p.grid = cps * p.n_sm;
     p.n_items = (int)items.size();
     p.n_tiles = n_tiles;
-    return set_smem_attr(tt, dyn_smem(tt, p.d.n_b));
+    return set_smem_attr(tt, dyn_smem(tt, p.d.n_b), p.d.k_mode == 2);
 }
 
 void free_plan(pt_batch_plan_s *p)
@@ -443,7 +477,8 @@ int pt_batch_plan_create(const pt_batch_desc *d, int autotune, pt_batch_plan *ou
     if (!d->t || !d->lc_offsets || !o.t0 || !o.P || !o.a || !o.inc || !d->k || !d->ld) return PT_ERR_ARG;
     if ((o.e == nullptr) != (o.w == nullptr)) return PT_ERR_ARG;
     if (!d->flux && !d->ssr) return PT_ERR_ARG;
-    if (d->k_mode != 0 && d->k_mode != 1) return PT_ERR_ARG;
+    if (d->k_mode < 0 || d->k_mode > 2) return PT_ERR_ARG;
+    if ((d->k_mode == 2) != (d->table != nullptr)) return PT_ERR_ARG;
     if (d->ssr && !d->y) return PT_ERR_ARG;
     if (!(d->t_exp >= 0.0 && d->t_exp < 1.0e30))
         return pt_internal::set_error(PT_ERR_DOMAIN, "pt_batch_plan_create", "exposure time must be finite and >= 0");
@@ -485,9 +520,9 @@ int pt_batch_plan_create(const pt_batch_desc *d, int autotune, pt_batch_plan *ou
         if (!autotune && tt != 128) continue;
         size_t smem = dyn_smem(tt, d->n_b);
         if (smem > 200 * 1024) continue;
-        st = set_smem_attr(tt, smem);
+        st = set_smem_attr(tt, smem, d->k_mode == 2);
         if (st) break;
-        int mx = max_ctas_per_sm(tt, smem);
+        int mx = max_ctas_per_sm(tt, smem, d->k_mode == 2);
         if (mx < 1) continue;
         int cands[4] = {mx, mx / 2, mx / 4, 1};
         for (int ci = 0; ci < 4 && st == PT_OK; ++ci) {

@@ -431,6 +431,35 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
     *ed = e_out;
 }
 
+// Bilinear interpolation of the tabulated Mandel-Agol terms (Sec. 2.2.3):
+// node (i, j) holds the terms at k_i = k_lo + i dk, z_j = j dz with
+// dz = (1 + k_hi) / (n_z - 1).  Out of transit (z >= 1 + k, also the
+// behind-the-star sentinel and NaN) the terms are zero; k is clamped to the
+// table's range.
+__device__ __forceinline__ void ma_interp(const float4 *tab, int n_k, int n_z, float k_lo, float k_hi,
+                                          float inv_dk, float inv_dz, float k, float z, float *le, float *ld,
+                                          float *ed)
+{
+    *le = 0.0f;
+    *ld = 0.0f;
+    *ed = 0.0f;
+    if (!(z < 1.0f + k)) return;
+    float fk = (fminf(fmaxf(k, k_lo), k_hi) - k_lo) * inv_dk;
+    int ik = min((int)fk, n_k - 2);
+    float wk = fk - (float)ik;
+    float fz = fminf(fmaxf(z, 0.0f) * inv_dz, (float)(n_z - 1));
+    int iz = min((int)fz, n_z - 2);
+    float wz = fz - (float)iz;
+    const float4 *r0 = tab + (size_t)ik * n_z + iz;
+    const float4 *r1 = r0 + n_z;
+    float4 a = __ldg(r0), b = __ldg(r0 + 1), c = __ldg(r1), d = __ldg(r1 + 1);
+    float a0 = fmaf(wz, b.x - a.x, a.x), a1 = fmaf(wz, b.y - a.y, a.y), a2 = fmaf(wz, b.z - a.z, a.z);
+    float c0 = fmaf(wz, d.x - c.x, c.x), c1 = fmaf(wz, d.y - c.y, c.y), c2 = fmaf(wz, d.z - c.z, c.z);
+    *le = fmaf(wk, c0 - a0, a0);
+    *ld = fmaf(wk, c1 - a1, a1);
+    *ed = fmaf(wk, c2 - a2, a2);
+}
+
 // Network coordinate across the ingress/egress band: theta = acos(1 - 2 s)
 // mapped to [-1, 1].  Near both contacts (s -> 0, s -> 1) the MA terms
 // behave like powers of sqrt(s) and sqrt(1 - s); in theta they are regular.

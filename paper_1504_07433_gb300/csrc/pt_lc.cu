@@ -138,35 +138,6 @@ struct LcArgs {
     float mk_lo, mk_hi, minv_dk, minv_dz;
 };
 
-// Bilinear interpolation of the tabulated Mandel-Agol terms (Sec. 2.2.3):
-// node (i, j) holds the terms at k_i = k_lo + i dk, z_j = j dz with
-// dz = (1 + k_hi) / (n_z - 1).  Out of transit (z >= 1 + k, also the
-// behind-the-star sentinel and NaN) the terms are zero; k is clamped to the
-// table's range.
-__device__ __forceinline__ void ma_interp(const float4 *tab, int n_k, int n_z, float k_lo, float k_hi,
-                                          float inv_dk, float inv_dz, float k, float z, float *le, float *ld,
-                                          float *ed)
-{
-    *le = 0.0f;
-    *ld = 0.0f;
-    *ed = 0.0f;
-    if (!(z < 1.0f + k)) return;
-    float fk = (fminf(fmaxf(k, k_lo), k_hi) - k_lo) * inv_dk;
-    int ik = min((int)fk, n_k - 2);
-    float wk = fk - (float)ik;
-    float fz = fminf(fmaxf(z, 0.0f) * inv_dz, (float)(n_z - 1));
-    int iz = min((int)fz, n_z - 2);
-    float wz = fz - (float)iz;
-    const float4 *r0 = tab + (size_t)ik * n_z + iz;
-    const float4 *r1 = r0 + n_z;
-    float4 a = __ldg(r0), b = __ldg(r0 + 1), c = __ldg(r1), d = __ldg(r1 + 1);
-    float a0 = fmaf(wz, b.x - a.x, a.x), a1 = fmaf(wz, b.y - a.y, a.y), a2 = fmaf(wz, b.z - a.z, a.z);
-    float c0 = fmaf(wz, d.x - c.x, c.x), c1 = fmaf(wz, d.y - c.y, c.y), c2 = fmaf(wz, d.z - c.z, c.z);
-    *le = fmaf(wk, c0 - a0, a0);
-    *ld = fmaf(wk, c1 - a1, a1);
-    *ed = fmaf(wk, c2 - a2, a2);
-}
-
 __device__ __forceinline__ float block_sum(float v, float *sred)
 {
 #pragma unroll
@@ -264,7 +235,7 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
             float z = pt::orbit_z<true>(r, dts, A.max_iter, &bad);
             if (bad) atomicAdd(&sbad, 1);
             if constexpr (INTERP)
-                ma_interp(A.mtab, A.mn_k, A.mn_z, A.mk_lo, A.mk_hi, A.minv_dk, A.minv_dz, r.k, z, &le, &ld, &ed);
+                pt::ma_interp(A.mtab, A.mn_k, A.mn_z, A.mk_lo, A.mk_hi, A.minv_dk, A.minv_dz, r.k, z, &le, &ld, &ed);
             else
                 pt::ma_terms(r.k, z, &le, &ld, &ed);
         }
@@ -1563,7 +1534,7 @@ __global__ void ma_terms_interp_kernel(const float4 *tab, int n_k, int n_z, floa
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float a, b, c;
-    ma_interp(tab, n_k, n_z, k_lo, k_hi, inv_dk, inv_dz, k[i], z[i], &a, &b, &c);
+    pt::ma_interp(tab, n_k, n_z, k_lo, k_hi, inv_dk, inv_dz, k[i], z[i], &a, &b, &c);
     if (le) le[i] = a;
     if (ld) ld[i] = b;
     if (ed) ed[i] = c;
@@ -1780,6 +1751,23 @@ struct pt_ma_table_s {
     int n_k, n_z;
     float4 *d_tab;   // [n_k][n_z]: (lambda_e, lambda_d + 2/3 Theta, eta_d, 0)
 };
+
+// The table's device view, for the batched path (pt_batch.cu).
+namespace pt_internal {
+bool ma_table_view(pt_ma_table t, const float4 **tab, int *n_k, int *n_z, float *k_lo, float *k_hi, float *inv_dk,
+                   float *inv_dz)
+{
+    if (!t || !t->d_tab) return false;
+    *tab = t->d_tab;
+    *n_k = t->n_k;
+    *n_z = t->n_z;
+    *k_lo = t->k_lo;
+    *k_hi = t->k_hi;
+    *inv_dk = t->inv_dk;
+    *inv_dz = t->inv_dz;
+    return true;
+}
+}  // namespace pt_internal
 
 struct pt_gim_plan_s {
     int N, n_j;

@@ -158,3 +158,39 @@ def test_batch_khat_mode_vs_oracle(torch_cuda, n_ss):
     # invalid mode refused
     with pytest.raises(pt.PTError):
         pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, want_flux=True, k_mode=2)
+
+
+@pytest.mark.parametrize("n_ss", [1, 3])
+def test_batch_interp_mode_vs_oracle(torch_cuda, n_ss):
+    """k_mode 2 (Sec. 2.2.3): each passband with its own k, the Mandel-Agol
+    terms read from the interpolation table, against the oracle's own
+    interpolated model on the same grid at 1e-6; its departure from the exact
+    model is the interpolation's own error (the oracle's interpolated model
+    against the oracle's exact one), to within the same 1e-6."""
+    torch = torch_cuda
+    import paper_1504_07433_gb300 as pt
+    wl = W.batched(n_walkers=9, n_pb=7, n_lc=4, len_lo=150, len_hi=600)
+    wl["n_ss"] = n_ss
+    wl["t_exp"] = 0.004 if n_ss > 1 else 0.0
+    t, orb, k, ld = gpu_inputs(wl)
+    y = torch.as_tensor(wl["y"], dtype=torch.float32, device="cuda")
+    grid = (0.09, 0.11, 128, 256)   # the workload's radius ratios, the paper's grid (Sec. 2.2.3)
+    table = pt.MATable(*grid)
+    plan = pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, n_ss=n_ss, t_exp=wl["t_exp"], y=y, want_flux=True,
+                        want_ssr=True, k_mode=2, table=table)
+    flux, ssr = plan.run()
+    torch.cuda.synchronize()
+    f = flux.cpu().numpy().astype(np.float64)
+    ref = oracle.lc_ma_interp(oracle.MATable(*grid), wl["t"], oracle_orbit(wl["orbit"]), f32(wl["k"]),
+                              f32(wl["ld"]), n_ss=n_ss, t_exp=wl["t_exp"])[0]
+    assert (ref < 1).mean() > 0.2
+    assert np.max(np.abs(f - ref)) <= TOL
+    yy = np.asarray(wl["y"], np.float32).astype(np.float64)
+    assert np.allclose(ssr.cpu().numpy(), np.sum((yy[None] - f) ** 2, axis=2), rtol=2e-5)
+    exact = _oracle(wl)
+    assert np.max(np.abs(f - exact)) <= np.max(np.abs(ref - exact)) + TOL
+    # a table goes with k_mode 2 only, and k_mode 2 needs one
+    with pytest.raises(pt.PTError):
+        pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, want_flux=True, k_mode=0, table=table)
+    with pytest.raises(pt.PTError):
+        pt.BatchPlan(t, wl["lc_offsets"], orb, k, ld, want_flux=True, k_mode=2)
