@@ -1029,7 +1029,7 @@ def main():
                 "paper_recursion_flops_ratio": paper_flops / flops}
 
     extra = {}
-    launches = 9 * K
+    launches = 10 * K   # MA: set-up, window, scan, pairs; Gimenez: table, coefficients, set-up, window, scan, series
     if not args.no_extra:
         extra["plain"], legs["plain"] = bench_plain(pt, torch, dev, stream)
         extra["ma_interp"], legs["ma_interp"] = bench_ma_interp(pt, torch, dev, stream, K, flush, t, orb, k, ld, wl, fm)

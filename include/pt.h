@@ -433,7 +433,15 @@ int pt_ma_quad_noalloc(const double *t_dev, int n_t, const pt_orbit *orb, const 
  * depth n_j: the recursion coefficients of G_j(nu+2, 1; x) and the A_{n,j}
  * of Eq. (gimemez_a), in device memory allocated by pt_gim_plan_create and
  * released by pt_gim_plan_destroy.  1 <= N <= 16, 2 <= n_j <= 512.
- * A plan may be used from any stream; it is read-only after creation.
+ * A plan may be used from any stream; its tables are read-only after
+ * creation.  The plan also owns a CUDA stream (the device's highest priority)
+ * and two events: pt_gimenez forks the per-geometry table recursion and the
+ * series coefficients, which depend on k alone, onto that stream at the start
+ * of the call (after all earlier work of the call's stream) and joins it
+ * before the evaluation kernel, so that they run beside the set-up and window
+ * kernels.  Calls from several host threads or streams may share a plan:
+ * their forked work runs in the order the calls were made.  Stream capture of
+ * a call captures the fork and the join.
  * ---------------------------------------------------------------------- */
 typedef struct pt_gim_plan_s *pt_gim_plan;
 

@@ -393,7 +393,7 @@ __device__ __forceinline__ DF df_mul(DF a, DF b)
 // its wide grid.
 constexpr int TABLE_GPC = 64;
 struct TableJob {
-    const GeomRec *rec;
+    const float *k;           // [n_geom] radius ratio of each geometry (the call's k)
     int n_geom, NP1, n_j;
     const double *A, *recb;   // the plan's A_{n,j} and recursion of G_j(nu+2, nu+1; x), FP64
     const float4 *coef;       // the plan's recursion of G_j(nu+2, 1; x), FP32
@@ -416,7 +416,7 @@ __device__ __forceinline__ void table_cta(const TableJob &J, int n, int gb)
     __syncthreads();
     const int g = gb * TABLE_GPC + threadIdx.x;
     if (threadIdx.x >= TABLE_GPC || g >= J.n_geom) return;
-    const double k = J.rec[g].k;
+    const double k = J.k[g];
     const DF x = df_of(1.0 - k / (1.0 + k));
     float4 *out = J.tab + ((size_t)g * J.NP1 + n) * n_j;
     DF gp = DF{0.0f, 0.0f}, gc = DF{1.0f, 0.0f};
@@ -551,6 +551,14 @@ __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A, TableJob J, i
     }
     id -= J.n_blocks;
     window_cta(A, id % n_tiles, id / n_tiles);
+}
+
+// The table CTAs alone: the Chebyshev path launches them on the plan's side
+// stream at the start of the call (they need only k), beside the set-up and
+// window kernels.
+__global__ void __launch_bounds__(TT) gim_table_kernel(TableJob J)
+{
+    table_cta(J, blockIdx.x % J.NP1, blockIdx.x / J.NP1);
 }
 
 // pref[g] = sum over g' < g of ceil(cnt[g'] / ppi); pref[n_geom] = total.
@@ -1775,6 +1783,14 @@ struct pt_gim_plan_s {
     double *d_A;      // [N+1][n_j]: A_{n,j}, FP64
     double *d_recb;   // [N+1][n_j][3]: recursion of G_j(nu+2, nu+1; x), FP64
     cudaEvent_t ev0, ev1;   // recorded around the series evaluation kernel when set (profiling)
+    // The table recursion and the Chebyshev coefficients depend on k alone:
+    // they run on this plan-owned stream (highest priority) beside the
+    // set-up, window and scan kernels of the call's stream, forked and joined
+    // by the two events; the mutex keeps a fork's record and wait together
+    // when host threads share the plan.
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
+    std::mutex fork_mu;
 };
 
 namespace {
@@ -1830,9 +1846,9 @@ int launch_zi(const GimArgs &A, const float *atab, int n_in, int n_edge, size_t 
     return check_launch("gim_zi_kernel");
 }
 
+// Chebyshev path, coefficient kernel for N + 1 orders.
 template <int NP1>
-int launch_cheb_t(const GimArgs &A, const float4 *T, float *dtab, size_t max_items, cudaEvent_t ev0, cudaEvent_t ev1,
-                  cudaStream_t s)
+int launch_cheb_coef_t(const GimArgs &A, const float4 *T, float *dtab, cudaStream_t s)
 {
     // coefficients: one warp per (geometry, order), rows padded to DS
     // floats (the warps past order N write the padding zeros)
@@ -1849,8 +1865,15 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, float *dtab, size_t max_ite
     else if (S <= 12) PT_COEF_LAUNCH(12);
     else PT_COEF_LAUNCH(16);
 #undef PT_COEF_LAUNCH
-    int st = check_launch("gim_cheb_coef_kernel");
-    if (st) return st;
+    return check_launch("gim_cheb_coef_kernel");
+}
+
+// Chebyshev path, evaluation kernel (persistent) for N + 1 orders.
+template <int NP1>
+int launch_cheb_eval_t(const GimArgs &A, float *dtab, size_t max_items, cudaEvent_t ev0, cudaEvent_t ev1,
+                       cudaStream_t s)
+{
+    int st = PT_OK;
     // evaluation: persistent
     const size_t smem = gim_cheb_smem(A.n_j, A.N, A.n_ss);
     static thread_local size_t configured = 0;
@@ -1878,29 +1901,42 @@ int launch_cheb_t(const GimArgs &A, const float4 *T, float *dtab, size_t max_ite
     return PT_OK;
 }
 
-// Chebyshev path: coefficient and evaluation kernels, for N + 1 orders.
-int launch_cheb(const GimArgs &A, const float4 *T, float *dtab, size_t max_items, cudaEvent_t ev0, cudaEvent_t ev1,
-                cudaStream_t s)
-{
-    switch (A.N + 1) {
-    case 2: return launch_cheb_t<2>(A, T, dtab, max_items, ev0, ev1, s);
-    case 3: return launch_cheb_t<3>(A, T, dtab, max_items, ev0, ev1, s);
-    case 4: return launch_cheb_t<4>(A, T, dtab, max_items, ev0, ev1, s);
-    case 5: return launch_cheb_t<5>(A, T, dtab, max_items, ev0, ev1, s);
-    case 6: return launch_cheb_t<6>(A, T, dtab, max_items, ev0, ev1, s);
-    case 7: return launch_cheb_t<7>(A, T, dtab, max_items, ev0, ev1, s);
-    case 8: return launch_cheb_t<8>(A, T, dtab, max_items, ev0, ev1, s);
-    case 9: return launch_cheb_t<9>(A, T, dtab, max_items, ev0, ev1, s);
-    case 10: return launch_cheb_t<10>(A, T, dtab, max_items, ev0, ev1, s);
-    case 11: return launch_cheb_t<11>(A, T, dtab, max_items, ev0, ev1, s);
-    case 12: return launch_cheb_t<12>(A, T, dtab, max_items, ev0, ev1, s);
-    case 13: return launch_cheb_t<13>(A, T, dtab, max_items, ev0, ev1, s);
-    case 14: return launch_cheb_t<14>(A, T, dtab, max_items, ev0, ev1, s);
-    case 15: return launch_cheb_t<15>(A, T, dtab, max_items, ev0, ev1, s);
-    case 16: return launch_cheb_t<16>(A, T, dtab, max_items, ev0, ev1, s);
-    default: return launch_cheb_t<17>(A, T, dtab, max_items, ev0, ev1, s);
+// Chebyshev path dispatch over N + 1 = 2 .. 17 orders.
+#define PT_NP1_DISPATCH(CALL)                                                                                       \
+    switch (A.N + 1) {                                                                                              \
+    case 2: return CALL(2);                                                                                         \
+    case 3: return CALL(3);                                                                                         \
+    case 4: return CALL(4);                                                                                         \
+    case 5: return CALL(5);                                                                                         \
+    case 6: return CALL(6);                                                                                         \
+    case 7: return CALL(7);                                                                                         \
+    case 8: return CALL(8);                                                                                         \
+    case 9: return CALL(9);                                                                                         \
+    case 10: return CALL(10);                                                                                       \
+    case 11: return CALL(11);                                                                                       \
+    case 12: return CALL(12);                                                                                       \
+    case 13: return CALL(13);                                                                                       \
+    case 14: return CALL(14);                                                                                       \
+    case 15: return CALL(15);                                                                                       \
+    case 16: return CALL(16);                                                                                       \
+    default: return CALL(17);                                                                                       \
     }
+
+int launch_cheb_coef(const GimArgs &A, const float4 *T, float *dtab, cudaStream_t s)
+{
+#define PT_CALL(V) launch_cheb_coef_t<V>(A, T, dtab, s)
+    PT_NP1_DISPATCH(PT_CALL)
+#undef PT_CALL
 }
+
+int launch_cheb_eval(const GimArgs &A, float *dtab, size_t max_items, cudaEvent_t ev0, cudaEvent_t ev1,
+                     cudaStream_t s)
+{
+#define PT_CALL(V) launch_cheb_eval_t<V>(A, dtab, max_items, ev0, ev1, s)
+    PT_NP1_DISPATCH(PT_CALL)
+#undef PT_CALL
+}
+#undef PT_NP1_DISPATCH
 
 }  // namespace
 
@@ -2324,7 +2360,14 @@ int pt_gim_plan_create(int N, int n_j, pt_gim_plan *out)
     p->d_A = nullptr;
     p->d_recb = nullptr;
     p->ev0 = p->ev1 = nullptr;
-    cudaError_t e = cudaMalloc(&p->d_coef, cnt * sizeof(float4));
+    p->side = nullptr;
+    p->ev_fork = p->ev_join = nullptr;
+    int prio_lo = 0, prio_hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, prio_hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_coef, cnt * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_A, cnt * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_recb, cnt * 3 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_coef, hcoef, cnt * sizeof(float4), cudaMemcpyHostToDevice);
@@ -2337,6 +2380,9 @@ int pt_gim_plan_create(int N, int n_j, pt_gim_plan *out)
         cudaFree(p->d_coef);
         cudaFree(p->d_A);
         cudaFree(p->d_recb);
+        if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+        if (p->ev_join) cudaEventDestroy(p->ev_join);
+        if (p->side) cudaStreamDestroy(p->side);
         delete p;
         return set_cuda_error(e, "pt_gim_plan_create");
     }
@@ -2358,6 +2404,9 @@ int pt_gim_plan_destroy(pt_gim_plan p)
     cudaFree(p->d_coef);
     cudaFree(p->d_A);
     cudaFree(p->d_recb);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->side) cudaStreamDestroy(p->side);
     delete p;
     return PT_OK;
 }
@@ -2413,9 +2462,8 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     float2 *tsplit = (float2 *)(wb + L.tsplit);
     float4 *T = (float4 *)(wb + L.T);
     int *cnt = (int *)(wb + L.cnt);
-    st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, cnt, s);
-    if (st) return st;
     float *atab = (float *)(wb + L.atab);
+    float *dtab = (float *)(wb + L.dtab);
     GimArgs A;
     memset(&A, 0, sizeof(A));
     A.tsplit = tsplit;
@@ -2439,7 +2487,7 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     A.ppi = GS_THREADS;   // work items of GS_THREADS listed pairs
     A.n_bad = n_bad;
     TableJob J;
-    J.rec = rec;
+    J.k = k;
     J.n_geom = n_geom;
     J.NP1 = NP1;
     J.n_j = plan->n_j;
@@ -2448,19 +2496,32 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
     J.coef = plan->d_coef;
     J.tab = T;
     J.n_blocks = NP1 * ((n_geom + TABLE_GPC - 1) / TABLE_GPC);
-    const size_t tsm = gim_table_smem(plan->n_j);
-    if (tsm > 48 * 1024) {
-        static thread_local size_t tsm_configured = 0;
-        if (tsm > tsm_configured) {
-            cudaError_t e = cudaFuncSetAttribute(gim_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)tsm);
-            if (e != cudaSuccess) return set_cuda_error(e, "gim_window_kernel smem attribute");
-            tsm_configured = tsm;
+    const size_t tsm = gim_table_smem(plan->n_j);   // at most 24 KB (n_j <= 512): no opt-in needed
+    if (!zi) {
+        // the table recursion and the Chebyshev coefficients depend on k
+        // alone: forked onto the plan's side stream (after all earlier work
+        // of the call's stream), joined before the evaluation kernel
+        cudaError_t e;
+        {
+            std::lock_guard<std::mutex> lk(plan->fork_mu);
+            e = cudaEventRecord(plan->ev_fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->side, plan->ev_fork, 0);
         }
+        if (e != cudaSuccess) return set_cuda_error(e, "pt_gimenez fork");
+        gim_table_kernel<<<(unsigned)J.n_blocks, TT, tsm, plan->side>>>(J);
+        st = check_launch("gim_table_kernel");
+        if (st) return st;
+        st = launch_cheb_coef(A, T, dtab, plan->side);
+        if (st) return st;
+        e = cudaEventRecord(plan->ev_join, plan->side);
+        if (e != cudaSuccess) return set_cuda_error(e, "pt_gimenez join");
+        J.n_blocks = 0;   // the window launch without table CTAs
     }
+    st = launch_setup(t, n_t, orb, k, k_per_band, n_b, t_exp, rec, tsplit, cnt, s);
+    if (st) return st;
     const size_t n_cta = (size_t)J.n_blocks + (size_t)n_tiles * gy;
     if (n_cta > 0x7fffffffULL) return PT_ERR_ARG;
-    gim_window_kernel<<<(unsigned)n_cta, TT, tsm, s>>>(A, J, n_tiles);
+    gim_window_kernel<<<(unsigned)n_cta, TT, J.n_blocks ? tsm : 0, s>>>(A, J, n_tiles);
     st = check_launch("gim_window_kernel");
     if (st) return st;
     if (zi) {
@@ -2468,15 +2529,17 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
         st = check_launch("gim_zi_table_kernel");
         if (st) return st;
     }
-    float *dtab = (float *)(wb + L.dtab);
     gim_scan_kernel<<<1, 1024, 0, s>>>(cnt, A.rec, A.t_exp, n_geom, A.ppi, true, A.pref, A.gord, A.ctr);
     st = check_launch("gim_scan_kernel");
     if (st) return st;
     const size_t max_items = (size_t)n_geom * ((n_t + GS_THREADS - 1) / GS_THREADS);
-    if (zi)
+    if (zi) {
         st = launch_zi(A, atab, n_in, n_edge, smem, max_items, s);
-    else
-        st = launch_cheb(A, T, dtab, max_items, plan->ev0, plan->ev1, s);
+    } else {
+        cudaError_t e = cudaStreamWaitEvent(s, plan->ev_join, 0);
+        if (e != cudaSuccess) return set_cuda_error(e, "pt_gimenez join");
+        st = launch_cheb_eval(A, dtab, max_items, plan->ev0, plan->ev1, s);
+    }
     if (st) return st;
     if (ssr) st = launch_ssr_rows(A.flux, y, wt, n_t, n_b, (size_t)orb->n_v * n_b, (float *)(wb + L.part), ssr, s);
     return st;
