@@ -319,6 +319,54 @@ def test_graph_capture_and_workspace_reuse(torch_cuda):
     plan.close()
 
 
+def test_plan_shared_by_host_threads(torch_cuda):
+    """Two host threads share one plan, each with its own stream and work
+    buffer and its own radius ratios, calls interleaved: the plan forks the
+    table and coefficient work of every call onto its own stream, and each
+    call still gives bitwise the flux of a call made alone."""
+    import threading
+    import paper_1504_07433_gb300 as pt
+    torch = torch_cuda
+    wl = W.long_cadence(n_v=12, n_t=4000)
+    wl["ld"] = wl["ld_gim"]
+    t, orb, k, ld = gpu_inputs(wl)
+    plan = pt.GimenezPlan(8, 64)
+    n_v, n_t = k.numel(), t.numel()
+    ks = [k, (k * 1.07).contiguous()]
+    refs = []
+    for kk in ks:
+        f, _ = pt.gimenez(plan, t, orb, kk, ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"])
+        torch.cuda.synchronize()
+        refs.append(f.clone())
+    outs = [[None] * 6 for _ in ks]
+    errors = []
+
+    def worker(i):
+        try:
+            s = torch.cuda.Stream()
+            work = torch.empty(plan.work_bytes(n_t, n_v, 1), dtype=torch.uint8, device="cuda")
+            with torch.cuda.stream(s):
+                for r in range(6):
+                    f = torch.empty_like(refs[i])
+                    pt.gimenez(plan, t, orb, ks[i], ld, n_ss=wl["n_ss"], t_exp=wl["t_exp"], work=work, flux=f)
+                    outs[i][r] = f
+            s.synchronize()
+        except Exception as e:   # reported below: a thread's failure must fail the test
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(ks))]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize()
+    assert not errors, errors
+    for i in range(len(ks)):
+        for f in outs[i]:
+            assert torch.equal(f, refs[i])
+    plan.close()
+
+
 def test_misaligned_workspace_rejected(torch_cuda):
     """A work buffer that does not start on a 16-byte boundary is refused
     (PT_ERR_WORKSPACE) before any kernel is launched."""
