@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(1024) gim_scan_kernel(const int *cnt, const Ge
 // shuffles); the table row sits in the warp's shared memory, read by
 // broadcast.  Warps for the row padding (orders N + 1 .. DS - 1) write zeros.
 // ---------------------------------------------------------------------------
-constexpr int CW_WARPS = 4;   // warps per CTA of the coefficient kernel
+constexpr int CW_WARPS = 1;   // warps per CTA of the coefficient kernel (one: the scheduler spreads the chains evenly)
 
 template <int S>
 __global__ void __launch_bounds__(32 * CW_WARPS) gim_cheb_coef_kernel(const float4 *gtab, int NP1, int n_j, int DS,
