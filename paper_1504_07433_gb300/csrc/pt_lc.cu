@@ -434,6 +434,71 @@ __device__ __forceinline__ void table_cta(const TableJob &J, int n, int gb)
 
 size_t gim_table_smem(int n_j) { return (size_t)n_j * (sizeof(float4) + 4 * sizeof(DF)); }
 
+// The same table from the standalone launch (the Chebyshev path's side
+// stream), with the chain threads doing only the recurrence: a chain runs
+// alone on its scheduler, so its time is the length of its instruction
+// stream.  Per CTA: order n, TABLE_GPC2 geometries.  All threads first form
+// r1_j + r2_j x of every geometry and step, the chain threads (one per
+// geometry) then run G_{j+1} = (r1 + r2 x) G_j + r3 G_{j-1} and keep each
+// G_j, and all threads finally form T_{n,j} = A_{n,j} G_j^2 and store the
+// packed rows.  The double-float operations are those of table_cta, so the
+// table is bitwise the same.
+constexpr int TABLE_GPC2 = 16;
+
+size_t gim_table2_smem(int n_j)
+{
+    return (size_t)n_j * (sizeof(float4) + 4 * sizeof(DF) + 2 * TABLE_GPC2 * sizeof(DF)) + TABLE_GPC2 * sizeof(DF);
+}
+
+__device__ __forceinline__ void table_cta2(const TableJob &J, int n, int gb)
+{
+    extern __shared__ __align__(16) unsigned char tsm[];
+    const int n_j = J.n_j;
+    float4 *scf = reinterpret_cast<float4 *>(tsm);   // [n_j]
+    DF *sA = reinterpret_cast<DF *>(scf + n_j);      // [n_j]
+    DF *srb = sA + n_j;                              // [n_j][3]
+    DF *sal = srb + 3 * n_j;                         // [TABLE_GPC2][n_j]: r1_j + r2_j x
+    DF *sG = sal + TABLE_GPC2 * n_j;                 // [TABLE_GPC2][n_j]: G_j
+    DF *sx = sG + TABLE_GPC2 * n_j;                  // [TABLE_GPC2]: x = 1 - b
+    const int tid = threadIdx.x;
+    const int g0 = gb * TABLE_GPC2;
+    const int ng = min(TABLE_GPC2, J.n_geom - g0);
+    for (int i = tid; i < n_j; i += blockDim.x) {
+        scf[i] = J.coef[(size_t)n * n_j + i];
+        sA[i] = df_of(J.A[(size_t)n * n_j + i]);
+    }
+    for (int i = tid; i < 3 * n_j; i += blockDim.x) srb[i] = df_of(J.recb[(size_t)n * n_j * 3 + i]);
+    if (tid < ng) {
+        const double k = J.k[g0 + tid];
+        sx[tid] = df_of(1.0 - k / (1.0 + k));
+    }
+    __syncthreads();
+    for (int j = tid; j < n_j; j += blockDim.x)
+        for (int gl = 0; gl < ng; ++gl) sal[gl * n_j + j] = df_add(srb[3 * j], df_mul(srb[3 * j + 1], sx[gl]));
+    __syncthreads();
+    if (tid < ng) {
+        const DF *al = sal + tid * n_j;
+        DF *G = sG + tid * n_j;
+        DF gp = DF{0.0f, 0.0f}, gc = DF{1.0f, 0.0f};
+        for (int j = 0; j < n_j; ++j) {
+            G[j] = gc;
+            const DF gn = df_add(df_mul(al[j], gc), df_mul(srb[3 * j + 2], gp));
+            gp = gc;
+            gc = gn;
+        }
+    }
+    __syncthreads();
+    for (int j = tid; j < n_j; j += blockDim.x) {
+        const float4 c = scf[j];
+        const float r3n = (j + 1 < n_j) ? scf[j + 1].z : 0.0f;
+        for (int gl = 0; gl < ng; ++gl) {
+            const DF gc = sG[gl * n_j + j];
+            const DF t = df_mul(df_mul(sA[j], gc), gc);
+            J.tab[((size_t)(g0 + gl) * J.NP1 + n) * n_j + j] = make_float4(c.x, c.y, r3n, t.h + t.l);
+        }
+    }
+}
+
 // One CTA covers TT times x GW_VT geometries.  The first pass of the window
 // test (as pt::maybe_in_window, but with its margin bounded once per tile and
 // geometry from the tile's largest |t_h|) costs a subtraction, a product, a
@@ -553,12 +618,12 @@ __global__ void __launch_bounds__(TT) gim_window_kernel(GimArgs A, TableJob J, i
     window_cta(A, id % n_tiles, id / n_tiles);
 }
 
-// The table CTAs alone: the Chebyshev path launches them on the plan's side
-// stream at the start of the call (they need only k), beside the set-up and
-// window kernels.
+// The table alone (table_cta2): the Chebyshev path launches it on the plan's
+// side stream at the start of the call (it needs only k), beside the set-up
+// and window kernels.
 __global__ void __launch_bounds__(TT) gim_table_kernel(TableJob J)
 {
-    table_cta(J, blockIdx.x % J.NP1, blockIdx.x / J.NP1);
+    table_cta2(J, blockIdx.x % J.NP1, blockIdx.x / J.NP1);
 }
 
 // pref[g] = sum over g' < g of ceil(cnt[g'] / ppi); pref[n_geom] = total.
@@ -2508,7 +2573,15 @@ static int gimenez_impl(pt_gim_plan plan, int n_in, int n_edge, const double *t,
             if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->side, plan->ev_fork, 0);
         }
         if (e != cudaSuccess) return set_cuda_error(e, "pt_gimenez fork");
-        gim_table_kernel<<<(unsigned)J.n_blocks, TT, tsm, plan->side>>>(J);
+        const size_t tsm2 = gim_table2_smem(plan->n_j);
+        static thread_local size_t tsm2_configured = 0;
+        if (tsm2 > 48 * 1024 && tsm2 > tsm2_configured) {
+            e = cudaFuncSetAttribute(gim_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm2);
+            if (e != cudaSuccess) return set_cuda_error(e, "gim_table_kernel smem attribute");
+            tsm2_configured = tsm2;
+        }
+        const int n_tb = NP1 * ((n_geom + TABLE_GPC2 - 1) / TABLE_GPC2);
+        gim_table_kernel<<<(unsigned)n_tb, TT, tsm2, plan->side>>>(J);
         st = check_launch("gim_table_kernel");
         if (st) return st;
         st = launch_cheb_coef(A, T, dtab, plan->side);
