@@ -447,7 +447,8 @@ constexpr int TABLE_GPC2 = 16;
 
 size_t gim_table2_smem(int n_j)
 {
-    return (size_t)n_j * (sizeof(float4) + 4 * sizeof(DF) + 2 * TABLE_GPC2 * sizeof(DF)) + TABLE_GPC2 * sizeof(DF);
+    return (size_t)n_j * (sizeof(float4) + 4 * sizeof(DF)) + 2 * (size_t)TABLE_GPC2 * (n_j + 1) * sizeof(DF) +
+           TABLE_GPC2 * sizeof(DF);
 }
 
 __device__ __forceinline__ void table_cta2(const TableJob &J, int n, int gb)
@@ -457,9 +458,12 @@ __device__ __forceinline__ void table_cta2(const TableJob &J, int n, int gb)
     float4 *scf = reinterpret_cast<float4 *>(tsm);   // [n_j]
     DF *sA = reinterpret_cast<DF *>(scf + n_j);      // [n_j]
     DF *srb = sA + n_j;                              // [n_j][3]
-    DF *sal = srb + 3 * n_j;                         // [TABLE_GPC2][n_j]: r1_j + r2_j x
-    DF *sG = sal + TABLE_GPC2 * n_j;                 // [TABLE_GPC2][n_j]: G_j
-    DF *sx = sG + TABLE_GPC2 * n_j;                  // [TABLE_GPC2]: x = 1 - b
+    // rows of n_j + 1: the chain lanes, one geometry each, read and write
+    // their rows at the same step without bank conflicts
+    const int rs = n_j + 1;
+    DF *sal = srb + 3 * n_j;                         // [TABLE_GPC2][n_j + 1]: r1_j + r2_j x
+    DF *sG = sal + TABLE_GPC2 * rs;                  // [TABLE_GPC2][n_j + 1]: G_j
+    DF *sx = sG + TABLE_GPC2 * rs;                   // [TABLE_GPC2]: x = 1 - b
     const int tid = threadIdx.x;
     const int g0 = gb * TABLE_GPC2;
     const int ng = min(TABLE_GPC2, J.n_geom - g0);
@@ -474,11 +478,11 @@ __device__ __forceinline__ void table_cta2(const TableJob &J, int n, int gb)
     }
     __syncthreads();
     for (int j = tid; j < n_j; j += blockDim.x)
-        for (int gl = 0; gl < ng; ++gl) sal[gl * n_j + j] = df_add(srb[3 * j], df_mul(srb[3 * j + 1], sx[gl]));
+        for (int gl = 0; gl < ng; ++gl) sal[gl * rs + j] = df_add(srb[3 * j], df_mul(srb[3 * j + 1], sx[gl]));
     __syncthreads();
     if (tid < ng) {
-        const DF *al = sal + tid * n_j;
-        DF *G = sG + tid * n_j;
+        const DF *al = sal + tid * rs;
+        DF *G = sG + tid * rs;
         DF gp = DF{0.0f, 0.0f}, gc = DF{1.0f, 0.0f};
         for (int j = 0; j < n_j; ++j) {
             G[j] = gc;
@@ -492,7 +496,7 @@ __device__ __forceinline__ void table_cta2(const TableJob &J, int n, int gb)
         const float4 c = scf[j];
         const float r3n = (j + 1 < n_j) ? scf[j + 1].z : 0.0f;
         for (int gl = 0; gl < ng; ++gl) {
-            const DF gc = sG[gl * n_j + j];
+            const DF gc = sG[gl * rs + j];
             const DF t = df_mul(df_mul(sA[j], gc), gc);
             J.tab[((size_t)(g0 + gl) * J.NP1 + n) * n_j + j] = make_float4(c.x, c.y, r3n, t.h + t.l);
         }
