@@ -28,7 +28,7 @@ int set_error(int status, const char *where, const char *msg);   // pt_lc.cu
 
 namespace {
 
-constexpr int TB = 256;
+constexpr int TB = 128;
 constexpr float PI_F = 3.14159265358979f;
 
 // cel(kc, 1, a, b) for two (a, b) pairs sharing kc and p = 1 (so the whole
@@ -426,7 +426,7 @@ __device__ __forceinline__ bool tile_meets_window(const pt::GeomRec &g, float tm
 }
 
 
-__global__ void __launch_bounds__(TB, 3) ma_bwd_kernel(BwdArgs A)
+__global__ void __launch_bounds__(TB, 6) ma_bwd_kernel(BwdArgs A)
 {
     __shared__ VecConst sc;
     __shared__ float sred[TB / 32][10];
