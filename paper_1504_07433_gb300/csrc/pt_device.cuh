@@ -64,6 +64,52 @@ __device__ __forceinline__ float fast_sqrt(float x)
     return x > 0.0f ? x * rsqrtf(x) : 0.0f;
 }
 
+// One-instruction hardware approximations (PTX rcp.approx.ftz, sqrt.approx.ftz:
+// about one ulp, denormal inputs and results flushed to zero).  Without the
+// .ftz form each call also carries the scaling that handles denormals.  The
+// Mandel-Agol core uses them only where its arguments are normal numbers or
+// exact zeros by construction (stated at each use).
+__device__ __forceinline__ float rcp_a(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_a(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// atan2(y, x) for y >= 0 (an angle in [0, pi]), for the lens angles of the
+// Mandel-Agol terms.  r = min(y, |x|) / max(y, |x|) lies in [0, 1] and
+// atan(r) = r P(r^2) with P of degree 8, fitted to atan(r)/r on [0, 1] by
+// Lawson's iteratively reweighted least squares (towards the minimax fit;
+// csrc/atan_poly.py recomputes the coefficients): 1.4e-8 absolute in FP64,
+// about 1.2e-7 evaluated in FP32.  Then atan2 = pi/2 - atan(r) when y > |x|,
+// and pi minus that when x < 0.  Both arguments zero give 0.
+__device__ __forceinline__ float atan2_pos(float y, float x)
+{
+    const float ax = fabsf(x);
+    const float mx = fmaxf(y, ax), mn = fminf(y, ax);
+    const float r = mx > 0.0f ? mn * rcp_a(mx) : 0.0f;   // mx is 0 or a normal number here
+    const float s = r * r;
+    float q = 2.903584391e-03f;
+    q = fmaf(q, s, -1.628314145e-02f);
+    q = fmaf(q, s, 4.303959757e-02f);
+    q = fmaf(q, s, -7.533697039e-02f);
+    q = fmaf(q, s, 1.065468788e-01f);
+    q = fmaf(q, s, -1.420713663e-01f);
+    q = fmaf(q, s, 1.999305487e-01f);
+    q = fmaf(q, s, -3.333309293e-01f);
+    q = fmaf(q, s, 1.0f);
+    float t = r * q;
+    if (y > ax) t = 0.5f * PT_PI_F - t;
+    if (x < 0.0f) t = PT_PI_F - t;
+    return t;
+}
+
 // First pass of the window test, in plain FP32: false only when t - t0 - nP
 // is certainly outside [win_lo, win_hi].  One FMA does the reduction with
 // the same epoch n as reduce_time; against the double-float result it drops
@@ -123,9 +169,10 @@ __device__ __forceinline__ void sincos_near0(float h, float *s, float *c)
 // passes warm[3] = {dE, dM, dE/dM} of the previous solution (warm[0] NaN for
 // none); the start dE + (dM' - dM) dE/dM is then off by ~e (dM' - dM)^2 / 2,
 // so one Newton step usually converges.  The solution is written back.
-// FAST takes the Newton quotient with __fdividef (its denominator
-// 1 - e cos E lies in [1 - e, 1 + e]) and the final root as x * rsqrtf(x):
-// about one ulp more in z.  ROT takes sin and cos of dE/2 at the solution
+// FAST takes the Newton quotient with the one-instruction reciprocal (its
+// denominator 1 - e cos E lies in [1 - e, 1 + e]) and the final root with the
+// one-instruction square root (an argument below 2^-126, a separation under
+// 1e-19, gives 0): about one ulp more in z.  ROT takes sin and cos of dE/2 at the solution
 // from the last step's values (below) instead of a second series; the
 // per-supersample loops of the pair-list kernels gain from it, while in the
 // batched and tile kernels the extra live values cost more than the series.
@@ -137,7 +184,7 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
         sincos_near0(r.nang * dt, &s, &c);
         if (c <= 0.0f) return PT_ZBEHIND;
         float ci = r.cosi * c;
-        return r.a * (FAST ? fast_sqrt(fmaf(s, s, ci * ci)) : sqrtf(fmaf(s, s, ci * ci)));
+        return r.a * (FAST ? sqrt_a(fmaf(s, s, ci * ci)) : sqrtf(fmaf(s, s, ci * ci)));
     }
     float dM = r.nang * dt;
     float dE = (warm && warm[0] == warm[0]) ? fmaf(dM - warm[1], warm[2], warm[0]) : dM / (1.0f - r.ecE);
@@ -149,7 +196,7 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
         float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
         float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
         if (FAST) {
-            dEdM = __fdividef(1.0f, Fp);
+            dEdM = rcp_a(Fp);
             step = F * dEdM;
         } else {
             step = F / Fp;
@@ -189,7 +236,7 @@ __device__ __forceinline__ float orbit_z(const GeomRec &r, float dt, int max_ite
     float V = r.Vtr + (r.Vs * dC + r.Vc * dS);
     if (V <= 0.0f) return PT_ZBEHIND;
     float Vi = V * r.cosi;
-    return FAST ? fast_sqrt(fmaf(U, U, Vi * Vi)) : sqrtf(fmaf(U, U, Vi * Vi));
+    return FAST ? sqrt_a(fmaf(U, U, Vi * Vi)) : sqrtf(fmaf(U, U, Vi * Vi));
 }
 
 
@@ -234,15 +281,17 @@ __device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsig
     return d;
 }
 
-__device__ __forceinline__ void cel2(float kc, float a1, float b1, float rho, float a2, float *r1,
+__device__ __forceinline__ void cel2(float kc, float a1, float b1, float srho, float a2, float *r1,
                                      float *r2)
 {
-    // lanes: (first integral, second integral)
-    unsigned long long A = f2_pack(a1, a2), B = f2_pack(b1, 0.0f), P = f2_pack(1.0f, fast_sqrt(rho));
+    // lanes: (first integral, second integral); srho = sqrt(rho).  The lanes'
+    // p start at 1 and sqrt(rho) >= 1 and only grow, kc in (0, 1] and e = kc m
+    // stay normal numbers, so the .ftz approximations never meet a denormal.
+    unsigned long long A = f2_pack(a1, a2), B = f2_pack(b1, 0.0f), P = f2_pack(1.0f, srho);
     float m = 1.0f, e = kc;
 #pragma unroll 1
     for (int it = 0; it < 10; ++it) {
-        const unsigned long long ip = f2_pack(__fdividef(1.0f, f2_lo(P)), __fdividef(1.0f, f2_hi(P)));
+        const unsigned long long ip = f2_pack(rcp_a(f2_lo(P)), rcp_a(f2_hi(P)));
         const unsigned long long F = A;
         A = f2_fma(B, ip, A);
         const unsigned long long G = f2_mul(f2_pack(e, e), ip);
@@ -252,27 +301,27 @@ __device__ __forceinline__ void cel2(float kc, float a1, float b1, float rho, fl
         float g = m;
         m = kc + m;
         if (fabsf(g - kc) <= g * 3e-4f) break;
-        kc = 2.0f * fast_sqrt(e);
+        kc = 2.0f * sqrt_a(e);
         e = kc * m;
     }
-    *r1 = __fdividef((0.5f * PT_PI_F) * fmaf(f2_lo(A), m, f2_lo(B)), m * (m + f2_lo(P)));
-    *r2 = __fdividef((0.5f * PT_PI_F) * fmaf(f2_hi(A), m, f2_hi(B)), m * (m + f2_hi(P)));
+    *r1 = (0.5f * PT_PI_F) * fmaf(f2_lo(A), m, f2_lo(B)) * rcp_a(m * (m + f2_lo(P)));
+    *r2 = (0.5f * PT_PI_F) * fmaf(f2_hi(A), m, f2_hi(B)) * rcp_a(m * (m + f2_hi(P)));
 }
 
 // cel2's loop carrying K = cel(kc, 1, 1, 1) and E = cel(kc, 1, 1, kc^2) in place
 // of one combination of them (cel with p = 1 is linear in (a, b), so
 // cel(kc, 1, cK + cE, cK + cE kc^2) = cK K + cE E), for callers that also need
 // K and E themselves.
-__device__ __forceinline__ void cel3(float kc, float rho, float a2, float *K, float *E, float *r2)
+__device__ __forceinline__ void cel3(float kc, float srho, float a2, float *K, float *E, float *r2)
 {
     float p1 = 1.0f;
-    float p2 = fast_sqrt(rho);
+    float p2 = srho;   // argument ranges as in cel2
     float aK = 1.0f, bK = 1.0f, aE = 1.0f, bE = kc * kc, b2 = 0.0f;
     float m = 1.0f, e = kc;
 #pragma unroll 1
     for (int it = 0; it < 10; ++it) {
-        float ip1 = __fdividef(1.0f, p1);
-        float ip2 = __fdividef(1.0f, p2);
+        float ip1 = rcp_a(p1);
+        float ip2 = rcp_a(p2);
         float g = e * ip1;
         float f = aK;
         aK = fmaf(bK, ip1, aK);
@@ -289,13 +338,13 @@ __device__ __forceinline__ void cel3(float kc, float rho, float a2, float *K, fl
         g = m;
         m = kc + m;
         if (fabsf(g - kc) <= g * 3e-4f) break;
-        kc = 2.0f * fast_sqrt(e);
+        kc = 2.0f * sqrt_a(e);
         e = kc * m;
     }
-    const float den = __fdividef(0.5f * PT_PI_F, m * (m + p1));
+    const float den = (0.5f * PT_PI_F) * rcp_a(m * (m + p1));
     *K = fmaf(aK, m, bK) * den;
     *E = fmaf(aE, m, bE) * den;
-    *r2 = __fdividef((0.5f * PT_PI_F) * fmaf(a2, m, b2), m * (m + p2));
+    *r2 = (0.5f * PT_PI_F) * fmaf(a2, m, b2) * rcp_a(m * (m + p2));
 }
 
 // ---------------------------------------------------------------------------
@@ -318,7 +367,15 @@ __device__ __forceinline__ void cel3(float kc, float rho, float a2, float *K, fl
 //   lambda_2: cK' = (b-1)(p^3 - p^2 z - p z^2 + 2p + z^3 - 4z)/(p+z),
 //             cR = -12 q z p / (a b)
 // so the brace is cel(kc, 1, cK'+cE, cK'+cE kc^2) + cel(kc, rho, cR, 0), two
-// bounded integrals evaluated in one shared loop (cel2).
+// bounded integrals evaluated in one shared loop (cel2).  With a = (z-p)^2,
+// b = (z+p)^2 and q = -(z-p)(z+p) these reduce exactly to
+//   lambda_1: sqrt(rho) = 1/|z-p|,        cR = 3 (z+p)(1-a)/(z-p),
+//   lambda_2: sqrt(rho) = (z+p)/|z-p|,    cR = 12 z p / ((z-p)(z+p)),
+// which the kernel evaluates (fewer roundings; z = p is a separate case).
+// Reciprocals and square roots are the one-instruction approximations.  For
+// p >= 1e-15 every argument they get is a normal number or zero: d and z - p
+// are 0 (separate cases) or at least an ulp of p, z or 1, and the products
+// formed from them stay far above 2^-126.
 // Exact special cases of Mandel & Agol's Table 1 that the general formulas
 // cannot evaluate (z = 1 - p, z = p, p = z = 1/2, star covered) are taken
 // separately; near them the general formulas stay accurate in FP32.
@@ -347,24 +404,21 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
     float oma = (1.0f - z + p) * (1.0f + z - p);
     float bm1 = d * (1.0f + z + p);
     float zmp = z - p;
-    float a = zmp * zmp;
-    float b = (z + p) * (z + p);
-    float q = -zmp * (p + z);
     float eta2 = 0.5f * p2 * (p2 + 2.0f * z2);
     bool inside = d < 0.0f;
 
     // lens geometry: only the partial (and contact) cases need it
     float le_part = p2, eta1 = eta2;
     if (!inside) {
-        float fa = fast_sqrt(oma * bm1);                 // 4 x triangle area
-        float k1 = atan2f(fa, 1.0f - p2 + z2);
-        float k0 = atan2f(fa, p2 + z2 - 1.0f);
+        float fa = sqrt_a(oma * bm1);                    // 4 x triangle area (oma, bm1 >= 0)
+        float k1 = atan2_pos(fa, 1.0f - p2 + z2);
+        float k0 = atan2_pos(fa, p2 + z2 - 1.0f);
         le_part = (p2 * k0 + k1 - 0.5f * fa) * (1.0f / pi);
         eta1 = (k1 + 2.0f * eta2 * k0 - 0.25f * (1.0f + 5.0f * p2 + z2) * fa) * (0.5f / pi);
     }
 
     // parameters of the shared elliptic evaluation
-    float kc, cKp, cE, rho = 1.0f, cR = 0.0f, pref, cst = 0.0f;
+    float kc, cKp, cE, srho = 1.0f, cR = 0.0f, pref, cst = 0.0f;
     bool need_cel = true;
     float e_out = inside ? eta2 : eta1;
     if (d == 0.0f) {                                 // case 4: lambda_5, z = 1 - p
@@ -396,32 +450,32 @@ __device__ __forceinline__ void ma_terms(float p, float z, float *le, float *ld,
             e_out = eta1;
         }
     } else if (inside) {                             // cases 3, 9: lambda_2
-        kc = fast_sqrt(__fdividef(-bm1, oma));
-        cKp = __fdividef(bm1 * (p2 * p - p2 * z - p * z2 + 2.0f * p + z2 * z - 4.0f * z), p + z);
+        kc = sqrt_a(-bm1 * rcp_a(oma));
+        cKp = bm1 * (p2 * p - p2 * z - p * z2 + 2.0f * p + z2 * z - 4.0f * z) * rcp_a(p + z);
         cE = oma * (z2 + 7.0f * p2 - 4.0f);
-        rho = __fdividef(b, a);
-        cR = __fdividef(-12.0f * q * z * p, a * b);
-        pref = __fdividef(2.0f, 9.0f * pi * fast_sqrt(oma));
+        srho = (p + z) * rcp_a(fabsf(zmp));
+        cR = (12.0f * z * p) * rcp_a(zmp * (z + p));
+        pref = 2.0f * rcp_a(9.0f * pi * sqrt_a(oma));
     } else {                                         // cases 2, 8: lambda_1
-        kc = fast_sqrt(__fdividef(bm1, 4.0f * z * p));
+        kc = sqrt_a(bm1 * rcp_a(4.0f * z * p));
         cKp = -bm1 * (6.0f * p2 + 2.0f * p * z - 3.0f);
         cE = 4.0f * p * z * (z2 + 7.0f * p2 - 4.0f);
-        rho = __fdividef(1.0f, a);
-        cR = __fdividef(-3.0f * q * oma, a);
-        pref = __fdividef(1.0f, 9.0f * pi * fast_sqrt(p * z));
+        srho = rcp_a(fabsf(zmp));
+        cR = (3.0f * (p + z) * oma) * rcp_a(zmp);
+        pref = rcp_a(9.0f * pi * sqrt_a(p * z));
     }
     float lam = cst;
     if (need_cel) {
         float r1, r2;
         if (KE && d != 0.0f && zmp != 0.0f) {
             float K, E;
-            cel3(kc, rho, cR, &K, &E, &r2);
+            cel3(kc, srho, cR, &K, &E, &r2);
             r1 = fmaf(cKp, K, cE * E);
             *Kout = K;
             *Eout = E;
             *have_ke = true;
         } else {
-            cel2(kc, cKp + cE, fmaf(cE, kc * kc, cKp), rho, cR, &r1, &r2);
+            cel2(kc, cKp + cE, fmaf(cE, kc * kc, cKp), srho, cR, &r1, &r2);
         }
         lam = fmaf(pref, r1 + r2, cst);
     }
