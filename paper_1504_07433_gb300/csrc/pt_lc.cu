@@ -191,9 +191,9 @@ __device__ __forceinline__ void phase_a(const LcArgs &A, GeomRec *srec, float (*
     __syncthreads();
 }
 
-__device__ __forceinline__ float ss_offset(float t_exp, int s, int n_ss)
+__device__ __forceinline__ float ss_offset(float t_exp, int s, float inv_nss)
 {
-    return t_exp * (((float)s + 0.5f) / (float)n_ss - 0.5f);
+    return t_exp * (((float)s + 0.5f) * inv_nss - 0.5f);   // inv_nss = 1 / n_ss
 }
 
 // ---------------------------------------------------------------------------
@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
     const int nss = A.n_ss;
     const int G = TT / nss;
     const int units = G * nss;
+    const float inv_nss = 1.0f / (float)nss;
 
     // Phase B: (pair, supersample) units
 #pragma unroll 1
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
             int code = squeue[item];
             int vl = code / TT, ti = code % TT;
             const GeomRec &r = srec[vl];
-            float dts = sdt[vl][ti] + ss_offset(A.t_exp, s, nss);
+            float dts = sdt[vl][ti] + ss_offset(A.t_exp, s, inv_nss);
             bool bad = false;
             float z = pt::orbit_z<true>(r, dts, A.max_iter, &bad);
             if (bad) atomicAdd(&sbad, 1);
@@ -262,7 +263,6 @@ __global__ void __launch_bounds__(TT) ma_lc_kernel(LcArgs A)
     // Phase C: limb darkening per passband, stores and residuals
     const int t = blockIdx.x * TT + tl;
     const bool tv = t < A.n_t;
-    const float inv_nss = 1.0f / (float)nss;
 #pragma unroll 1
     for (int vl = 0; vl < VT_MA; ++vl) {
         int g = blockIdx.y * VT_MA + vl;
@@ -1077,12 +1077,14 @@ __global__ void __launch_bounds__(GS_THREADS, 5) gim_cheb_kernel(GimArgs A, cons
 #pragma unroll 1
                 for (int s = sb0; s < s1; ++s) {
                     bool bad = false;
-                    const float z = pt::orbit_z<true, true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
+                    const float z = pt::orbit_z<true, true>(srec, dt + ss_offset(A.t_exp, s, inv_nss), A.max_iter, &bad, warm);
                     if (bad) ++nbad;
                     if (z < 1.0f + kk) {
-                        const float cz = z / (1.0f + kk);
+                        // z < 1 + k; the rounded reciprocal may put cz an ulp above 1
+                        const float cz = fminf(z * pt::rcp_a(1.0f + kk), 1.0f);
                         const float x = cz * cz;
-                        syq[c * GS_THREADS + tid] = make_float2(fmaf(2.0f, x, -1.0f), sqrtf((1.0f - cz) * (1.0f + cz)));
+                        // (1 - cz)(1 + cz) is 0 or at least ~2^-24: a normal argument
+                        syq[c * GS_THREADS + tid] = make_float2(fmaf(2.0f, x, -1.0f), pt::sqrt_a((1.0f - cz) * (1.0f + cz)));
                         ++c;
                     }
                 }
@@ -1310,7 +1312,7 @@ __global__ void __launch_bounds__(GS_THREADS) gim_zi_kernel(GimArgs A, const flo
 #pragma unroll 1
             for (int s = 0; s < nss; ++s) {
                 bool bad = false;
-                float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
+                float z = pt::orbit_z<true>(srec, dt + ss_offset(A.t_exp, s, inv_nss), A.max_iter, &bad, warm);
                 if (bad) ++nbad;
                 if (!(z < 1.0f + kk)) continue;   // out of transit: alpha = 0
                 int i0;
@@ -1377,7 +1379,7 @@ size_t gim_zi_smem(int N, int nz) { return (size_t)(N + 1) * (nz + GS_THREADS) *
 constexpr int MA_PPI = 128;   // pairs per work item (= threads per CTA)
 constexpr int MA_SSB = 16;    // supersamples per batch
 
-__global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
+__global__ void __launch_bounds__(MA_PPI, 8) ma_pairs_kernel(GimArgs A)
 {
     __shared__ GeomRec srec;
     __shared__ int sitem, sgeom, sfirst, scount, sbad;
@@ -1445,7 +1447,7 @@ __global__ void __launch_bounds__(MA_PPI) ma_pairs_kernel(GimArgs A)
 #pragma unroll 1
                 for (int s = sb0; s < s1; ++s) {
                     bool bad = false;
-                    const float z = pt::orbit_z<true, true>(srec, dt + ss_offset(A.t_exp, s, nss), A.max_iter, &bad, warm);
+                    const float z = pt::orbit_z<true, true>(srec, dt + ss_offset(A.t_exp, s, inv_nss), A.max_iter, &bad, warm);
                     if (bad) ++nbad;
                     if (z < 1.0f + kk && kk > 0.0f) {
                         szp[c * MA_PPI + tid] = z;
