@@ -40,7 +40,7 @@ __device__ __forceinline__ void ellke(float kc, float *K, float *E)
     float p = 1.0f, m = 1.0f, e = kc;
 #pragma unroll 1
     for (int it = 0; it < 10; ++it) {
-        float ip = __fdividef(1.0f, p);
+        float ip = pt::rcp_a(p);   // p, kc, e, m normal throughout (as in pt::cel2)
         float g = e * ip;
         float f = a1;
         a1 = fmaf(b1, ip, a1);
@@ -52,10 +52,10 @@ __device__ __forceinline__ void ellke(float kc, float *K, float *E)
         g = m;
         m = kc + m;
         if (fabsf(g - kc) <= g * 3e-4f) break;
-        kc = 2.0f * sqrtf(e);
+        kc = 2.0f * pt::sqrt_a(e);
         e = kc * m;
     }
-    float den = 1.0f / (m * (m + p));
+    float den = pt::rcp_a(m * (m + p));
     *K = (0.5f * PI_F) * fmaf(a1, m, b1) * den;
     *E = (0.5f * PI_F) * fmaf(a2, m, b2) * den;
 }
@@ -93,7 +93,7 @@ __device__ __forceinline__ float s2c2_int(float m, float K, float E)
         for (int n = 22; n >= 0; --n) s = fmaf(s, m, C.a[n]);
         return s;
     }
-    return ((2.0f - m) * E - 2.0f * (1.0f - m) * K) / (3.0f * m * m);
+    return ((2.0f - m) * E - 2.0f * (1.0f - m) * K) * pt::rcp_a(3.0f * m * m);   // m >= 1/2
 }
 
 // Overlap integrals I (x pi-free form: I_1 = pi le, I_mu = pi ld', I_mu2 =
@@ -109,11 +109,12 @@ __device__ __forceinline__ void overlap_derivs(float p, float z, float *d, bool 
     float dd = (z - 1.0f) + p;
     float al = 1.0f - z * z - p * p;
     if (dd < 0.0f) {                                   // full circle inside the star
-        float m = 4.0f * z * p / oma;
-        float kc = sqrtf(-dd * (1.0f + z + p) / oma);
+        // oma, -dd and z p are normal numbers here (as in pt::ma_terms)
+        const float ioma = pt::rcp_a(oma);
+        float m = 4.0f * z * p * ioma;
         float K = Kin, E = Ein;
-        if (!have_ke) ellke(kc, &K, &E);
-        float so = sqrtf(oma);
+        if (!have_ke) ellke(pt::sqrt_a(-dd * (1.0f + z + p) * ioma), &K, &E);
+        float so = pt::sqrt_a(oma);
         d[0] = 2.0f * PI_F * p;
         d[2] = 4.0f * p * so * E;
         d[3] = -p * 4.0f * so * m * s2c2_int(m, K, E);
@@ -122,11 +123,12 @@ __device__ __forceinline__ void overlap_derivs(float p, float z, float *d, bool 
         return;
     }
     float bm1 = dd * (1.0f + z + p);
-    float fa = sqrtf(fmaxf(0.0f, oma * bm1));
-    float kap0 = atan2f(fa, p * p + z * z - 1.0f);
-    float ipz = 1.0f / (2.0f * p * z);
+    float fa = pt::sqrt_a(fmaxf(0.0f, oma * bm1));
+    float kap0 = pt::atan2_pos(fa, p * p + z * z - 1.0f);
+    float ipz = pt::rcp_a(2.0f * p * z);
     float sk = fa * ipz, ck = (p * p + z * z - 1.0f) * ipz;
-    float m1 = oma / (4.0f * z * p), mc1 = bm1 / (4.0f * z * p);
+    float m1 = 0.5f * oma * ipz, mc1 = 0.5f * bm1 * ipz;
+    const float szp = pt::sqrt_a(z * p);
     float K, E, mcK;
     if (dd == 0.0f) {                                  // contact with the limb from inside: m1 = 1
         E = 1.0f;
@@ -136,15 +138,15 @@ __device__ __forceinline__ void overlap_derivs(float p, float z, float *d, bool 
             K = Kin;
             E = Ein;
         } else {
-            ellke(sqrtf(mc1), &K, &E);
+            ellke(pt::sqrt_a(mc1), &K, &E);
         }
         mcK = mc1 * K;
     }
     float icos = -2.0f * sk, icos2 = kap0 + sk * ck;
     d[0] = 2.0f * p * kap0;
     d[1] = p * icos;
-    d[2] = 8.0f * p * sqrtf(z * p) * (E - mcK);
-    d[3] = -p * (4.0f / 3.0f) * sqrtf(4.0f * z * p) * ((2.0f * m1 - 1.0f) * E + mcK);
+    d[2] = 8.0f * p * szp * (E - mcK);
+    d[3] = -p * (8.0f / 3.0f) * szp * ((2.0f * m1 - 1.0f) * E + mcK);
     d[4] = p * (al * 2.0f * kap0 - 2.0f * z * p * icos);
     d[5] = p * (al * icos - 2.0f * z * p * icos2);
 }
@@ -155,6 +157,7 @@ struct VecConst {
     float ci, dci_a, dci_b, dci_e, dci_w;
     float dMtr_de, dMtr_dw;
     float k, u1, u2, c0, c2, D;
+    float invPD, inv3D, inv6D, ise;   // 1 / (pi D), 1 / (3 D), 1 / (6 D), 1 / se
 };
 
 __device__ void make_const(const pt_theta &th, int v, float half_exp, VecConst *c)
@@ -252,6 +255,10 @@ __device__ void make_const(const pt_theta &th, int v, float half_exp, VecConst *
     c->c0 = 1.0f - c->u1 - c->u2;
     c->c2 = c->u1 + 2.0f * c->u2;
     c->D = 1.0f - c->u1 * (1.0f / 3.0f) - c->u2 * (1.0f / 6.0f);
+    c->invPD = 1.0f / (PI_F * c->D);
+    c->inv3D = 1.0f / (3.0f * c->D);
+    c->inv6D = 1.0f / (6.0f * c->D);
+    c->ise = 1.0f / c->se;
 }
 
 // Flux and its gradient at one (time, supersample) point.
@@ -268,7 +275,7 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
         float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
         float F = (dE - r.ecE * sn) + (r.esE * omc - dM);
         float Fp = 1.0f - r.ecE * (1.0f - omc) + r.esE * sn;
-        float step = __fdividef(F, Fp);   // Fp lies in [1 - e, 1 + e]
+        float step = F * pt::rcp_a(Fp);   // Fp lies in [1 - e, 1 + e]
         dE -= step;
         if (fabsf(step) <= 4e-7f * fabsf(dE) + 1e-12f) {
             conv = true;
@@ -294,19 +301,19 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
     const float pi = PI_F;
     float I0 = pi * le, I1 = pi * ld, I2 = pi * (le - ed);
     float N = c.c0 * I0 + c.c2 * I1 - c.u2 * I2;
-    float invPD = 1.0f / (pi * c.D);
+    const float invPD = c.invPD;
     float f = 1.0f - N * invPD;
     float d[6];
     overlap_derivs(c.k, z, d, have_ke, Kc, Ec);
     float dFdk = -(c.c0 * d[0] + c.c2 * d[2] - c.u2 * d[4]) * invPD;
     float dFdz = -(c.c0 * d[1] + c.c2 * d[3] - c.u2 * d[5]) * invPD;
     g[6] = dFdk;
-    g[7] = -((I1 - I0) * invPD + N * invPD / (3.0f * c.D));
-    g[8] = -((2.0f * I1 - I0 - I2) * invPD + N * invPD / (6.0f * c.D));
+    g[7] = -((I1 - I0) * invPD + N * invPD * c.inv3D);
+    g[8] = -((2.0f * I1 - I0 - I2) * invPD + N * invPD * c.inv6D);
     // chain rule through the orbit
     float cE = r.cE + dC, sE = r.sE + dS;
     float a = r.a, e = c.e, se = c.se, sw = c.sw, cw = c.cw, ci = c.ci;
-    float iecE = 1.0f / (1.0f - e * cE);
+    float iecE = pt::rcp_a(1.0f - e * cE);   // in [1/(1+e), 1/(1-e)]
     float zinv = 1.0f / z;
     // i = 0 (t0), 1 (P): only M moves
     {
@@ -331,7 +338,7 @@ __device__ __forceinline__ float point_grad(const VecConst &c, float dts, float 
     {   // i = 4 (e)
         float dEi = (c.dMtr_de + sE) * iecE;
         float dX = -a * sE * dEi - a;
-        float dY = a * se * cE * dEi - a * e * sE / se;
+        float dY = a * se * cE * dEi - a * e * sE * c.ise;
         float dU = dX * cw - dY * sw;
         float dV = dX * sw + dY * cw;
         g[4] = dFdz * (U * dU + V * ci * ci * dV + V * V * ci * c.dci_e) * zinv;
