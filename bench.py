@@ -115,7 +115,7 @@ class ClockSampler:
 # DRAM traffic of one gim_cheb_kernel launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from its ncu capture, per vector of the long-cadence
 # workload, and the build it was taken on (null for any other depth)
-TRAFFIC = {"per_vector_bytes": (2.403072e6 + 6.144e3) / 128.0, "n_j": 192}
+TRAFFIC = {"per_vector_bytes": (2.398208e6 + 7.424e3) / 128.0, "n_j": 192}
 
 
 def whole_job_rate(ms_local, pts_per_rank, ws, device="cpu"):
