@@ -55,15 +55,6 @@ __device__ __forceinline__ float reduce_time(float th, float tl, const GeomRec &
     return d + lo;
 }
 
-// Square root through the hardware reciprocal square root (about one ulp
-// off the correctly rounded value; exact zero at 0).  The Mandel-Agol terms
-// use it, and __fdividef, where their arguments are bounded well inside the
-// normal range; the accuracy budget of those terms is ~1e-7 absolute.
-__device__ __forceinline__ float fast_sqrt(float x)
-{
-    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
-}
-
 // One-instruction hardware approximations (PTX rcp.approx.ftz, sqrt.approx.ftz:
 // about one ulp, denormal inputs and results flushed to zero).  Without the
 // .ftz form each call also carries the scaling that handles denormals.  The
