@@ -381,6 +381,18 @@ __device__ __forceinline__ DF df_mul(DF a, DF b)
     return df_norm(p, e);
 }
 
+// a b + c with one two-sum: the product's rounding error (fmaf), the two-sum
+// error of p + c_h, the cross terms and c_l go into the low part
+__device__ __forceinline__ DF df_mad(DF a, DF b, DF c)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p);
+    const float s = p + c.h;
+    const float bb = s - p;
+    const float err = (p - (s - bb)) + (c.h - bb);
+    return df_norm(s, fmaf(a.h, b.l, fmaf(a.l, b.h, c.l)) + (e + err));
+}
+
 // Gimenez per-geometry table for Clenshaw's summation: entry (n, j) packs the
 // z-recursion coefficients r1_j, r2_j, r3_{j+1} of G_j(nu+2, 1; x) with
 // T_{n,j} = A_{n,j} G_j(nu+2, nu+1; 1-b)^2, the z-independent factor of
@@ -483,11 +495,13 @@ __device__ __forceinline__ void table_cta2(const TableJob &J, int n, int gb)
     if (tid < ng) {
         const DF *al = sal + tid * rs;
         DF *G = sG + tid * rs;
-        DF gp = DF{0.0f, 0.0f}, gc = DF{1.0f, 0.0f};
+        // G_{j+1} = al_j G_j + r3_j G_{j-1}; q = r3_j G_{j-1} is formed one
+        // step ahead, so each step's dependent path is one df_mad
+        DF gc = DF{1.0f, 0.0f}, q = DF{0.0f, 0.0f};
         for (int j = 0; j < n_j; ++j) {
             G[j] = gc;
-            const DF gn = df_add(df_mul(al[j], gc), df_mul(srb[3 * j + 2], gp));
-            gp = gc;
+            const DF gn = df_mad(al[j], gc, q);
+            if (j + 1 < n_j) q = df_mul(srb[3 * (j + 1) + 2], gc);
             gc = gn;
         }
     }
