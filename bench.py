@@ -375,7 +375,7 @@ def bench_batched(pt, torch, dev, stream, K, flush, n_walkers=1024, modes=("ssr"
     return out, payload
 
 
-def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000, epochs=40, n_chk=1_000_000):
+def bench_surrogate(torch, dev, stream, n_infer=1_000_000_000, epochs=40, n_chk=10_000_000):
     """Surrogate network: trained here on 1e7 exact-kernel samples (40 epochs,
     the library's own kernels), error-bound table from 4e6 validation points,
     then 1e9 band points through pt_ma_surrogate (BF16 tensor cores + exact
